@@ -1,0 +1,275 @@
+"""Sequential CPU oracle for compact cuckoo and compact iceberg hash tables.
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. It wraps the plain C
+restatement of the paper's algorithms in ``oracle.c`` (Algorithm 4 and the
+Section 4.4 lookup for cuckoo, Algorithm 5 and the Section 2.3 lookup for
+iceberg, enumeration by k = pi^-1(a . r) of Section 2.4) and shares no code with
+the CUDA library.
+
+Parity status per function (see the tests that pin each one):
+  perm / perm_inv / address / remainder: pinned by brute-force bijectivity over
+      every key of a 16-bit space and by the round trip of Section 2.4; the
+      round function itself is a design reading (Section 4.3 does not fix it).
+  prec: pinned by the worked ranks of the slot-ordering figure (Appendix A).
+  iceberg_fop: pinned by Theorem 1 (a)-(e) on brute-force tiny tables and by
+      agreement with an independent restatement of Algorithm 1.
+  cuckoo_insert / cuckoo_find: pinned by set semantics on brute-force tiny
+      tables, the H=1 closed form (a plain bucketed table), and the exhaustive
+      lookup.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NOT_FOUND, FOUND, PUT, FULL, INVALID = 0, 1, 2, 3, 4
+CUCKOO, ICEBERG = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so with the host C compiler."""
+    src = os.path.join(_HERE, "oracle.c")
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(src)
+            and os.path.getmtime(_SO) >= os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        return _SO
+    tmp = _SO + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall",
+                           "-o", tmp, src])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("compact", ctypes.c_int),
+        ("key_bits", ctypes.c_int),
+        ("num_hashes", ctypes.c_int),
+        ("max_chain", ctypes.c_int),
+        ("wpb", ctypes.c_int),
+        ("fpw", ctypes.c_int * 2),
+        ("nb", ctypes.c_uint64 * 2),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_cfgp = ctypes.POINTER(Cfg)
+_sz = ctypes.c_size_t
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            u64, i = ctypes.c_uint64, ctypes.c_int
+            sig = {
+                "orc_cfg_check": (i, [_cfgp]),
+                "orc_perm": (u64, [_cfgp, i, i, u64]),
+                "orc_perm_inv": (u64, [_cfgp, i, i, u64]),
+                "orc_address": (u64, [_cfgp, i, i, u64]),
+                "orc_remainder": (u64, [_cfgp, i, i, u64]),
+                "orc_key_from": (u64, [_cfgp, i, i, u64, u64]),
+                "orc_perm_many": (None, [_cfgp, i, i, _u64p, _sz, _u64p, _u64p, _u64p, _u64p]),
+                "orc_prec": (i, [i, i, i, i]),
+                "orc_table_words": (u64, [_cfgp, i]),
+                "orc_slots_per_bucket": (i, [_cfgp, i]),
+                "orc_get_slot": (u64, [_cfgp, i, _u64p, u64, i]),
+                "orc_cuckoo_insert": (None, [_cfgp, _u64p, _u64p, _sz, _u8p, _u64p, _u64p, _u64p]),
+                "orc_cuckoo_find": (None, [_cfgp, _u64p, _u64p, _sz, _u8p, _u64p]),
+                "orc_cuckoo_find_exhaustive": (None, [_cfgp, _u64p, _u64p, _sz, _u8p]),
+                "orc_iceberg_fop": (None, [_cfgp, _u64p, _u64p, _u64p, _sz, _u8p, _u64p, _u64p]),
+                "orc_iceberg_find": (None, [_cfgp, _u64p, _u64p, _u64p, _sz, _u8p, _u64p]),
+                "orc_enumerate": (u64, [_cfgp, _u64p, _u64p, _u64p, u64]),
+                "orc_check_prefix": (u64, [_cfgp, i, _u64p]),
+                "orc_check_entries": (u64, [_cfgp, _u64p, _u64p]),
+                "orc_check_order_property": (u64, [_cfgp, _u64p, _u64p]),
+                "orc_check_cuckoo_chain": (u64, [_cfgp, _u64p]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p64(a: np.ndarray):
+    assert a.dtype == np.uint64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_u64p)
+
+
+def _p8(a: np.ndarray):
+    assert a.dtype == np.uint8 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_u8p)
+
+
+def _keys(keys) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(keys).astype(np.uint64))
+
+
+def make_cfg(kind: int, key_bits: int, nb0: int, nb1: int = 0, *,
+             compact: bool = True, fpw0: int = 1, fpw1: int = 1, wpb: int = 16,
+             num_hashes: int = 3, max_chain: int = 128, seed: int = 0) -> Cfg:
+    c = Cfg()
+    c.kind, c.compact, c.key_bits = kind, int(compact), key_bits
+    c.num_hashes, c.max_chain, c.wpb = num_hashes, max_chain, wpb
+    c.fpw[0], c.fpw[1] = fpw0, (fpw1 if kind == ICEBERG else 1)
+    c.nb[0], c.nb[1] = nb0, (nb1 if kind == ICEBERG else 0)
+    c.seed = seed & 0xFFFFFFFFFFFFFFFF
+    return c
+
+
+def check_cfg(*args, **kw) -> int:
+    """0 if the configuration (same arguments as Table) is usable."""
+    return int(lib().orc_cfg_check(ctypes.byref(make_cfg(*args, **kw))))
+
+
+class Table:
+    """A host-resident table of either kind, operated on sequentially.
+
+    kind: CUCKOO or ICEBERG. compact: quotiented remainders (True) or whole
+    keys in 64-bit slots. nb0 / nb1: bucket counts of level 0 (the cuckoo
+    table or iceberg primary) and level 1 (iceberg secondary). fpw0 / fpw1:
+    fields per 64-bit word. wpb: 64-bit words per bucket (16 = 128 bytes).
+    """
+
+    def __init__(self, kind: int, key_bits: int, nb0: int, nb1: int = 0, *,
+                 compact: bool = True, fpw0: int = 1, fpw1: int = 1, wpb: int = 16,
+                 num_hashes: int = 3, max_chain: int = 128, seed: int = 0):
+        c = make_cfg(kind, key_bits, nb0, nb1, compact=compact, fpw0=fpw0, fpw1=fpw1,
+                     wpb=wpb, num_hashes=num_hashes, max_chain=max_chain, seed=seed)
+        self.cfg = c
+        self._cp = ctypes.byref(c)
+        L = lib()
+        err = int(L.orc_cfg_check(self._cp))
+        if err:
+            raise ValueError(f"oracle: invalid table configuration (check {err})")
+        self.t0 = np.zeros(int(L.orc_table_words(self._cp, 0)), dtype=np.uint64)
+        n1 = int(L.orc_table_words(self._cp, 1)) if kind == ICEBERG else 0
+        self.t1 = np.zeros(max(n1, 1), dtype=np.uint64)
+        self.probes = 0
+        self.writes = 0
+
+    # -- permutation -------------------------------------------------------
+    def perm(self, level: int, j: int, k: int) -> int:
+        return int(lib().orc_perm(self._cp, level, j, k))
+
+    def perm_inv(self, level: int, j: int, p: int) -> int:
+        return int(lib().orc_perm_inv(self._cp, level, j, p))
+
+    def address(self, level: int, j: int, k: int) -> int:
+        return int(lib().orc_address(self._cp, level, j, k))
+
+    def remainder(self, level: int, j: int, k: int) -> int:
+        return int(lib().orc_remainder(self._cp, level, j, k))
+
+    def key_from(self, level: int, j: int, a: int, r: int) -> int:
+        return int(lib().orc_key_from(self._cp, level, j, a, r))
+
+    def perm_many(self, level: int, j: int, keys):
+        """Vectorised (perm, address, remainder, perm_inv(perm)) over keys."""
+        k = _keys(keys)
+        outs = [np.zeros(len(k), dtype=np.uint64) for _ in range(4)]
+        lib().orc_perm_many(self._cp, level, j, _p64(k), len(k), *[_p64(o) for o in outs])
+        return tuple(outs)
+
+    def slots_per_bucket(self, level: int) -> int:
+        return int(lib().orc_slots_per_bucket(self._cp, level))
+
+    def slot(self, level: int, bucket: int, y: int) -> int:
+        t = self.t0 if level == 0 else self.t1
+        return int(lib().orc_get_slot(self._cp, level, _p64(t), bucket, y))
+
+    # -- operations --------------------------------------------------------
+    def insert(self, keys):
+        """Cuckoo: Algorithm 4 per key. Iceberg: find-or-put. Returns
+        (status, dropped) for cuckoo and status for iceberg."""
+        k = _keys(keys)
+        st = np.zeros(len(k), dtype=np.uint8)
+        p, w = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        if self.cfg.kind == CUCKOO:
+            dr = np.zeros(len(k), dtype=np.uint64)
+            lib().orc_cuckoo_insert(self._cp, _p64(self.t0), _p64(k), len(k), _p8(st),
+                                    _p64(dr), ctypes.byref(p), ctypes.byref(w))
+            self.probes, self.writes = p.value, w.value
+            return st, dr
+        lib().orc_iceberg_fop(self._cp, _p64(self.t0), _p64(self.t1), _p64(k), len(k),
+                              _p8(st), ctypes.byref(p), ctypes.byref(w))
+        self.probes, self.writes = p.value, w.value
+        return st
+
+    def find_or_put(self, keys):
+        assert self.cfg.kind == ICEBERG
+        return self.insert(keys)
+
+    def find(self, keys):
+        k = _keys(keys)
+        st = np.zeros(len(k), dtype=np.uint8)
+        p = ctypes.c_uint64(0)
+        if self.cfg.kind == CUCKOO:
+            lib().orc_cuckoo_find(self._cp, _p64(self.t0), _p64(k), len(k), _p8(st),
+                                  ctypes.byref(p))
+        else:
+            lib().orc_iceberg_find(self._cp, _p64(self.t0), _p64(self.t1), _p64(k), len(k),
+                                   _p8(st), ctypes.byref(p))
+        self.probes = p.value
+        return st
+
+    def find_exhaustive(self, keys):
+        assert self.cfg.kind == CUCKOO
+        k = _keys(keys)
+        st = np.zeros(len(k), dtype=np.uint8)
+        lib().orc_cuckoo_find_exhaustive(self._cp, _p64(self.t0), _p64(k), len(k), _p8(st))
+        return st
+
+    def enumerate(self) -> np.ndarray:
+        L = lib()
+        n = int(L.orc_enumerate(self._cp, _p64(self.t0), _p64(self.t1), None, 0))
+        out = np.zeros(max(n, 1), dtype=np.uint64)
+        L.orc_enumerate(self._cp, _p64(self.t0), _p64(self.t1), _p64(out), n)
+        return out[:n]
+
+    # -- invariants --------------------------------------------------------
+    def check_prefix(self) -> int:
+        L = lib()
+        bad = int(L.orc_check_prefix(self._cp, 0, _p64(self.t0)))
+        if self.cfg.kind == ICEBERG:
+            bad += int(L.orc_check_prefix(self._cp, 1, _p64(self.t1)))
+        return bad
+
+    def check_entries(self) -> int:
+        return int(lib().orc_check_entries(self._cp, _p64(self.t0), _p64(self.t1)))
+
+    def check_order_property(self) -> int:
+        assert self.cfg.kind == ICEBERG
+        return int(lib().orc_check_order_property(self._cp, _p64(self.t0), _p64(self.t1)))
+
+    def check_cuckoo_chain(self) -> int:
+        assert self.cfg.kind == CUCKOO
+        return int(lib().orc_check_cuckoo_chain(self._cp, _p64(self.t0)))
+
+    def load_words(self, t0: np.ndarray, t1: np.ndarray | None = None):
+        """Replace the table contents with a dump (e.g. of a device table)."""
+        self.t0[:] = np.asarray(t0, dtype=np.uint64).reshape(-1)[: len(self.t0)]
+        if t1 is not None and self.cfg.kind == ICEBERG:
+            self.t1[:] = np.asarray(t1, dtype=np.uint64).reshape(-1)[: len(self.t1)]
+
+
+def prec(x1: int, y1: int, x2: int, y2: int) -> bool:
+    """Definition 1: (x1, y1) strictly precedes (x2, y2)."""
+    return bool(lib().orc_prec(x1, y1, x2, y2))

@@ -1,0 +1,681 @@
+/*
+ * oracle.c - sequential CPU oracle for compact bucketed cuckoo hashing and
+ * compact two-level iceberg hashing (Hegeman et al., "Compact Parallel Hash
+ * Tables on the GPU").
+ *
+ * TEST INFRASTRUCTURE: called only by the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark. Shares no code with the CUDA library.
+ * Every function is a plain sequential restatement of the paper's definition
+ * or algorithm, cited beside it.
+ *
+ * Readings of points the paper leaves open (each also listed in the design
+ * notes of the repository):
+ *   - Permutation (Section 4.3 says only "one-round Feistel"): with R = w - N,
+ *     split k into L = k >> R (N bits) and r = k mod 2^R. Then
+ *     pi(k) = ((L xor f(r)) << R) | r, with f(r) = (A*r + B) mod 2^64 >> (64-N),
+ *     A odd. A and B come from the splitmix64 sequence of the table seed.
+ *   - Address and remainder (Section 2.4): a(k) = first N bits of pi(k),
+ *     r(k) = the other R bits. For a bucket count nb that is not a power of
+ *     two (whole-key tables only) a(k) = (pi(k) * nb) >> w with N = ceil(log2 nb).
+ *   - Slot contents: cuckoo (r << 2) | (j + 1) (Section 2.2 stores (k, j));
+ *     iceberg primary (r << 1) | 1 (one bit marks occupancy, Section 5.1);
+ *     iceberg secondary (r << 2) | (i + 1), i the secondary choice
+ *     (Algorithm 1 stores (r_i(k), i - 1)). Whole-key tables store k in place
+ *     of r. The all-zero field is EMPTY.
+ *   - Cuckoo eviction choice (Algorithm 4: "pseudorandomly, or based on c, k"):
+ *     slot = (hi32(splitmix64(k, c)) * B) >> 32, k the key in hand at step c.
+ *   - Key 0 and keys >= 2^w are rejected as INVALID.
+ */
+#include "oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_GAMMA 0x9E3779B97F4A7C15ULL
+
+/* splitmix64 finaliser (Steele, Lea and Flood, OOPSLA 2014) */
+static uint64_t orc_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* output number idx (0-based) of the splitmix64 sequence whose state starts at s */
+static uint64_t orc_splitmix(uint64_t s, uint64_t idx)
+{
+    return orc_mix64(s + (idx + 1) * ORC_GAMMA);
+}
+
+static int orc_ceil_log2(uint64_t x)
+{
+    int n = 0;
+    while (n < 64 && (1ULL << n) < x)
+        n++;
+    return n;
+}
+
+static uint64_t orc_low_mask(int bits)
+{
+    return bits >= 64 ? ~0ULL : ((1ULL << bits) - 1);
+}
+
+static int orc_valid_key(const orc_cfg *c, uint64_t k)
+{
+    return k != 0 && (c->key_bits >= 64 || (k >> c->key_bits) == 0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Permutation pi_j and quotienting, Section 2.4 and Section 4.3             */
+/* ------------------------------------------------------------------------ */
+
+static int orc_addr_bits(const orc_cfg *c, int level)
+{
+    return orc_ceil_log2(c->nb[level]);
+}
+
+int orc_cfg_check(const orc_cfg *c)
+{
+    int levels = c->kind == 1 ? 2 : 1;
+    if (c->kind != 0 && c->kind != 1)
+        return 1;
+    if (c->key_bits < 2 || c->key_bits > 62)
+        return 2;
+    if (c->wpb < 1 || c->wpb > 16)
+        return 3;
+    if (c->kind == 0 && (c->num_hashes < 1 || c->num_hashes > 3 || c->max_chain < 1))
+        return 4;
+    for (int level = 0; level < levels; level++) {
+        int fpw = c->fpw[level];
+        uint64_t nb = c->nb[level];
+        int n = orc_addr_bits(c, level);
+        /* tag bits: cuckoo (j + 1) in 2 bits, iceberg primary 1, secondary 2 */
+        int tag = (c->kind == 1 && level == 0) ? 1 : 2;
+        int body = c->compact ? c->key_bits - n : c->key_bits;
+        if (fpw < 1 || fpw > 4)
+            return 5;
+        if (nb < 1 || n >= c->key_bits)
+            return 6;
+        if (c->compact && (nb & (nb - 1)) != 0)
+            return 7;
+        if (body + tag > 64 / fpw)
+            return 8;
+    }
+    return 0;
+}
+
+/* Feistel round function of permutation j on the given level */
+static uint64_t orc_round(const orc_cfg *c, int level, int j, uint64_t r)
+{
+    int n = orc_addr_bits(c, level);
+    uint64_t idx = 2 * (uint64_t)(4 * level + j);
+    uint64_t A = orc_splitmix(c->seed, idx) | 1ULL;
+    uint64_t B = orc_splitmix(c->seed, idx + 1);
+    if (n == 0)
+        return 0;
+    return (A * r + B) >> (64 - n);
+}
+
+uint64_t orc_perm(const orc_cfg *c, int level, int j, uint64_t k)
+{
+    int R = c->key_bits - orc_addr_bits(c, level);
+    uint64_t r = k & orc_low_mask(R);
+    uint64_t L = k >> R;
+    return ((L ^ orc_round(c, level, j, r)) << R) | r;
+}
+
+uint64_t orc_perm_inv(const orc_cfg *c, int level, int j, uint64_t p)
+{
+    int R = c->key_bits - orc_addr_bits(c, level);
+    uint64_t r = p & orc_low_mask(R);
+    uint64_t L = (p >> R) ^ orc_round(c, level, j, r);
+    return (L << R) | r;
+}
+
+/* a_j(k): the first N bits of pi_j(k); for a bucket count that is not a
+ * power of two, pi_j(k) scaled onto [0, nb) */
+uint64_t orc_address(const orc_cfg *c, int level, int j, uint64_t k)
+{
+    uint64_t p = orc_perm(c, level, j, k);
+    unsigned __int128 prod = (unsigned __int128)p * c->nb[level];
+    return (uint64_t)(prod >> c->key_bits);
+}
+
+/* r_j(k): the remaining w - N bits of pi_j(k) */
+uint64_t orc_remainder(const orc_cfg *c, int level, int j, uint64_t k)
+{
+    int R = c->key_bits - orc_addr_bits(c, level);
+    return orc_perm(c, level, j, k) & orc_low_mask(R);
+}
+
+/* k = pi_j^-1(a . r), Section 2.4 */
+uint64_t orc_key_from(const orc_cfg *c, int level, int j, uint64_t a,
+                      uint64_t r)
+{
+    int R = c->key_bits - orc_addr_bits(c, level);
+    return orc_perm_inv(c, level, j, (a << R) | r);
+}
+
+void orc_perm_many(const orc_cfg *c, int level, int j, const uint64_t *keys,
+                   size_t n, uint64_t *out_perm, uint64_t *out_addr,
+                   uint64_t *out_rem, uint64_t *out_back)
+{
+    for (size_t i = 0; i < n; i++) {
+        uint64_t p = orc_perm(c, level, j, keys[i]);
+        if (out_perm)
+            out_perm[i] = p;
+        if (out_addr)
+            out_addr[i] = orc_address(c, level, j, keys[i]);
+        if (out_rem)
+            out_rem[i] = orc_remainder(c, level, j, keys[i]);
+        if (out_back)
+            out_back[i] = orc_perm_inv(c, level, j, p);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Slot order, Definition 1 (Appendix A)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* (x1, y1) strictly precedes (x2, y2). x = 0 is the primary bucket, x = 1 and
+ * x = 2 the first and second secondary buckets. The definition lists the cases
+ * in which the order holds; since it is a total order, (2, y) precedes (1, x)
+ * exactly when (1, x) does not precede (2, y), i.e. when y <= x. */
+int orc_prec(int x1, int y1, int x2, int y2)
+{
+    if (x1 == x2)
+        return y1 < y2;
+    if (x1 == 0)
+        return 1;
+    if (x2 == 0)
+        return 0;
+    if (x1 == 1) /* x2 == 2 */
+        return y1 < y2;
+    return y1 <= y2; /* x1 == 2, x2 == 1 */
+}
+
+/* ------------------------------------------------------------------------ */
+/* Table geometry and slot access                                            */
+/* ------------------------------------------------------------------------ */
+
+uint64_t orc_table_words(const orc_cfg *c, int level)
+{
+    return c->nb[level] * (uint64_t)c->wpb;
+}
+
+int orc_slots_per_bucket(const orc_cfg *c, int level)
+{
+    return (uint64_t)c->wpb * c->fpw[level];
+}
+
+uint64_t orc_get_slot(const orc_cfg *c, int level, const uint64_t *table,
+                      uint64_t bucket, int y)
+{
+    int fpw = c->fpw[level];
+    int s = 64 / fpw;
+    uint64_t word = table[bucket * (uint64_t)c->wpb + (uint64_t)(y / fpw)];
+    return (word >> ((y % fpw) * s)) & orc_low_mask(s);
+}
+
+static void orc_set_slot(const orc_cfg *c, int level, uint64_t *table,
+                         uint64_t bucket, int y, uint64_t v)
+{
+    int fpw = c->fpw[level];
+    int s = 64 / fpw;
+    int sh = (y % fpw) * s;
+    uint64_t m = orc_low_mask(s) << sh;
+    uint64_t *w = &table[bucket * (uint64_t)c->wpb + (uint64_t)(y / fpw)];
+    *w = (*w & ~m) | ((v << sh) & m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Entry encodings                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* cuckoo slot content for key k placed through hash j: the pair (r_j(k), j) */
+static uint64_t orc_cuckoo_entry(const orc_cfg *c, int j, uint64_t k)
+{
+    uint64_t body = c->compact ? orc_remainder(c, 0, j, k) : k;
+    return (body << 2) | (uint64_t)(j + 1);
+}
+
+/* iceberg slot content r'_x(k) for x in {0, 1, 2} (Appendix A notation):
+ * r'_0 = r_0(k), r'_{1+i} = (r_{1+i}(k), i) */
+static uint64_t orc_iceberg_entry(const orc_cfg *c, int x, uint64_t k)
+{
+    if (x == 0) {
+        uint64_t body = c->compact ? orc_remainder(c, 0, 0, k) : k;
+        return (body << 1) | 1ULL;
+    } else {
+        uint64_t body = c->compact ? orc_remainder(c, 1, x - 1, k) : k;
+        return (body << 2) | (uint64_t)x;
+    }
+}
+
+/* bucket index and level of the (x, .) bucket of key k in an iceberg table */
+static uint64_t orc_iceberg_bucket(const orc_cfg *c, int x, uint64_t k)
+{
+    return x == 0 ? orc_address(c, 0, 0, k) : orc_address(c, 1, x - 1, k);
+}
+
+static const uint64_t *orc_level_table(int x, const uint64_t *t0,
+                                       const uint64_t *t1)
+{
+    return x == 0 ? t0 : t1;
+}
+
+static int orc_bucket_contains(const orc_cfg *c, int level,
+                               const uint64_t *table, uint64_t bucket,
+                               uint64_t entry)
+{
+    int B = orc_slots_per_bucket(c, level);
+    for (int y = 0; y < B; y++)
+        if (orc_get_slot(c, level, table, bucket, y) == entry)
+            return 1;
+    return 0;
+}
+
+static int orc_bucket_has_empty(const orc_cfg *c, int level,
+                                const uint64_t *table, uint64_t bucket)
+{
+    int B = orc_slots_per_bucket(c, level);
+    for (int y = 0; y < B; y++)
+        if (orc_get_slot(c, level, table, bucket, y) == 0)
+            return 1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cuckoo put, Algorithm 4, run sequentially                                 */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t orc_evict_slot(uint64_t k, int step, int B)
+{
+    uint64_t h = orc_splitmix(k, (uint64_t)step) >> 32;
+    return (h * (uint64_t)B) >> 32;
+}
+
+/* decode a cuckoo entry found in bucket a into (key, hash index) */
+static uint64_t orc_cuckoo_decode(const orc_cfg *c, uint64_t a, uint64_t e,
+                                  int *j_out)
+{
+    int j = (int)(e & 3) - 1;
+    *j_out = j;
+    if (c->compact)
+        return orc_key_from(c, 0, j, a, e >> 2);
+    return e >> 2;
+}
+
+static int orc_cuckoo_put(const orc_cfg *c, uint64_t *table, uint64_t k,
+                          uint64_t *dropped, uint64_t *probes,
+                          uint64_t *writes)
+{
+    int B = orc_slots_per_bucket(c, 0);
+    int j = 0;
+    for (int step = 1; step <= c->max_chain; step++) {
+        uint64_t a = orc_address(c, 0, j, k);
+        uint64_t e = orc_cuckoo_entry(c, j, k);
+        int y_empty = -1;
+        (*probes)++;
+        for (int y = 0; y < B; y++) {
+            if (orc_get_slot(c, 0, table, a, y) == 0) {
+                y_empty = y;
+                break;
+            }
+        }
+        (*writes)++;
+        if (y_empty >= 0) {
+            /* an empty slot: claim the first one */
+            orc_set_slot(c, 0, table, a, y_empty, e);
+            return ORC_PUT;
+        }
+        /* bucket full: swap (r, j) with the chosen slot, continue with the
+         * evicted key under its next hash function */
+        int y = (int)orc_evict_slot(k, step, B);
+        uint64_t old = orc_get_slot(c, 0, table, a, y);
+        orc_set_slot(c, 0, table, a, y, e);
+        int jo;
+        k = orc_cuckoo_decode(c, a, old, &jo);
+        j = (jo + 1) % c->num_hashes;
+    }
+    *dropped = k;
+    return ORC_FULL;
+}
+
+void orc_cuckoo_insert(const orc_cfg *c, uint64_t *table, const uint64_t *keys,
+                       size_t n, uint8_t *status, uint64_t *dropped,
+                       uint64_t *probes, uint64_t *writes)
+{
+    uint64_t p = 0, w = 0;
+    for (size_t i = 0; i < n; i++) {
+        uint64_t d = 0;
+        if (!orc_valid_key(c, keys[i])) {
+            status[i] = ORC_INVALID;
+        } else {
+            status[i] = (uint8_t)orc_cuckoo_put(c, table, keys[i], &d, &p, &w);
+        }
+        if (dropped)
+            dropped[i] = d;
+    }
+    if (probes)
+        *probes = p;
+    if (writes)
+        *writes = w;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cuckoo lookup, Section 4.4                                                */
+/* ------------------------------------------------------------------------ */
+
+void orc_cuckoo_find(const orc_cfg *c, const uint64_t *table,
+                     const uint64_t *keys, size_t n, uint8_t *status,
+                     uint64_t *probes)
+{
+    uint64_t p = 0;
+    for (size_t i = 0; i < n; i++) {
+        uint64_t k = keys[i];
+        if (!orc_valid_key(c, k)) {
+            status[i] = ORC_INVALID;
+            continue;
+        }
+        status[i] = ORC_NOT_FOUND;
+        for (int j = 0; j < c->num_hashes; j++) {
+            uint64_t a = orc_address(c, 0, j, k);
+            p++;
+            if (orc_bucket_contains(c, 0, table, a, orc_cuckoo_entry(c, j, k))) {
+                status[i] = ORC_FOUND;
+                break;
+            }
+            /* a bucket with a free slot ends the search: k would have been
+             * placed here before moving on to a_{j+1} */
+            if (orc_bucket_has_empty(c, 0, table, a))
+                break;
+        }
+    }
+    if (probes)
+        *probes = p;
+}
+
+void orc_cuckoo_find_exhaustive(const orc_cfg *c, const uint64_t *table,
+                                const uint64_t *keys, size_t n,
+                                uint8_t *status)
+{
+    for (size_t i = 0; i < n; i++) {
+        uint64_t k = keys[i];
+        if (!orc_valid_key(c, k)) {
+            status[i] = ORC_INVALID;
+            continue;
+        }
+        status[i] = ORC_NOT_FOUND;
+        for (int j = 0; j < c->num_hashes; j++)
+            if (orc_bucket_contains(c, 0, table, orc_address(c, 0, j, k),
+                                    orc_cuckoo_entry(c, j, k)))
+                status[i] = ORC_FOUND;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Iceberg find-or-put, Algorithm 5 (Appendix A), run sequentially           */
+/* ------------------------------------------------------------------------ */
+
+static int orc_iceberg_fop1(const orc_cfg *c, uint64_t *t0, uint64_t *t1,
+                            uint64_t k, uint64_t *probes, uint64_t *writes)
+{
+    int Bx[3] = {orc_slots_per_bucket(c, 0), orc_slots_per_bucket(c, 1),
+                 orc_slots_per_bucket(c, 1)};
+    uint64_t a[3], e[3];
+    for (int x = 0; x < 3; x++) {
+        a[x] = orc_iceberg_bucket(c, x, k);
+        e[x] = orc_iceberg_entry(c, x, k);
+    }
+    /* bucket probes the method needs: the primary alone decides when it
+     * holds k or has room (Algorithm 1, level 1); otherwise both secondaries */
+    if (orc_bucket_contains(c, 0, t0, a[0], e[0]) ||
+        orc_bucket_has_empty(c, 0, t0, a[0]))
+        *probes += 1;
+    else
+        *probes += 3;
+
+    /* found: some slot (x, y) of S holds r'_x(k) */
+    for (int x = 0; x < 3; x++)
+        for (int y = 0; y < Bx[x]; y++)
+            if (orc_get_slot(c, x ? 1 : 0, orc_level_table(x, t0, t1), a[x],
+                             y) == e[x])
+                return ORC_FOUND;
+    /* otherwise the prec-least empty slot of S, if any */
+    int bx = -1, by = -1;
+    for (int x = 0; x < 3; x++)
+        for (int y = 0; y < Bx[x]; y++) {
+            if (orc_get_slot(c, x ? 1 : 0, orc_level_table(x, t0, t1), a[x],
+                             y) != 0)
+                continue;
+            if (bx < 0 || orc_prec(x, y, bx, by)) {
+                bx = x;
+                by = y;
+            }
+        }
+    if (bx < 0)
+        return ORC_FULL;
+    orc_set_slot(c, bx ? 1 : 0, bx ? t1 : t0, a[bx], by, e[bx]);
+    (*writes)++;
+    return ORC_PUT;
+}
+
+void orc_iceberg_fop(const orc_cfg *c, uint64_t *t0, uint64_t *t1,
+                     const uint64_t *keys, size_t n, uint8_t *status,
+                     uint64_t *probes, uint64_t *writes)
+{
+    uint64_t p = 0, w = 0;
+    for (size_t i = 0; i < n; i++) {
+        if (!orc_valid_key(c, keys[i]))
+            status[i] = ORC_INVALID;
+        else
+            status[i] = (uint8_t)orc_iceberg_fop1(c, t0, t1, keys[i], &p, &w);
+    }
+    if (probes)
+        *probes = p;
+    if (writes)
+        *writes = w;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Iceberg lookup, Section 2.3 (levels 1 and 2)                              */
+/* ------------------------------------------------------------------------ */
+
+void orc_iceberg_find(const orc_cfg *c, const uint64_t *t0, const uint64_t *t1,
+                      const uint64_t *keys, size_t n, uint8_t *status,
+                      uint64_t *probes)
+{
+    uint64_t p = 0;
+    for (size_t i = 0; i < n; i++) {
+        uint64_t k = keys[i];
+        if (!orc_valid_key(c, k)) {
+            status[i] = ORC_INVALID;
+            continue;
+        }
+        uint64_t a0 = orc_iceberg_bucket(c, 0, k);
+        p++;
+        if (orc_bucket_contains(c, 0, t0, a0, orc_iceberg_entry(c, 0, k))) {
+            status[i] = ORC_FOUND;
+            continue;
+        }
+        if (orc_bucket_has_empty(c, 0, t0, a0)) {
+            status[i] = ORC_NOT_FOUND;
+            continue;
+        }
+        p += 2;
+        int hit = 0;
+        for (int x = 1; x <= 2; x++)
+            if (orc_bucket_contains(c, 1, t1, orc_iceberg_bucket(c, x, k),
+                                    orc_iceberg_entry(c, x, k)))
+                hit = 1;
+        status[i] = hit ? ORC_FOUND : ORC_NOT_FOUND;
+    }
+    if (probes)
+        *probes = p;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Enumerate: k = pi^-1(a . r) for every stored entry (Section 2.4)          */
+/* ------------------------------------------------------------------------ */
+
+/* key held by entry e found in bucket a of the given level; -1 tag on error */
+static uint64_t orc_decode(const orc_cfg *c, int level, uint64_t a, uint64_t e,
+                           int *x_out)
+{
+    if (c->kind == 0) {
+        int j;
+        uint64_t k = orc_cuckoo_decode(c, a, e, &j);
+        *x_out = j;
+        return k;
+    }
+    if (level == 0) {
+        *x_out = 0;
+        return c->compact ? orc_key_from(c, 0, 0, a, e >> 1) : e >> 1;
+    }
+    int x = (int)(e & 3);
+    *x_out = x;
+    if (x < 1 || x > 2)
+        return 0;
+    return c->compact ? orc_key_from(c, 1, x - 1, a, e >> 2) : e >> 2;
+}
+
+static int orc_levels(const orc_cfg *c)
+{
+    return c->kind == 1 ? 2 : 1;
+}
+
+uint64_t orc_enumerate(const orc_cfg *c, const uint64_t *t0,
+                       const uint64_t *t1, uint64_t *out, uint64_t cap)
+{
+    uint64_t cnt = 0;
+    for (int level = 0; level < orc_levels(c); level++) {
+        const uint64_t *t = level ? t1 : t0;
+        int B = orc_slots_per_bucket(c, level);
+        for (uint64_t a = 0; a < c->nb[level]; a++)
+            for (int y = 0; y < B; y++) {
+                uint64_t e = orc_get_slot(c, level, t, a, y);
+                if (e == 0)
+                    continue;
+                int x;
+                uint64_t k = orc_decode(c, level, a, e, &x);
+                if (cnt < cap)
+                    out[cnt] = k;
+                cnt++;
+            }
+    }
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Invariant checkers                                                        */
+/* ------------------------------------------------------------------------ */
+
+uint64_t orc_check_prefix(const orc_cfg *c, int level, const uint64_t *table)
+{
+    uint64_t bad = 0;
+    int B = orc_slots_per_bucket(c, level);
+    for (uint64_t a = 0; a < c->nb[level]; a++) {
+        int seen_empty = 0;
+        for (int y = 0; y < B; y++) {
+            uint64_t e = orc_get_slot(c, level, table, a, y);
+            if (e == 0)
+                seen_empty = 1;
+            else if (seen_empty) {
+                bad++;
+                break;
+            }
+        }
+    }
+    return bad;
+}
+
+uint64_t orc_check_entries(const orc_cfg *c, const uint64_t *t0,
+                           const uint64_t *t1)
+{
+    uint64_t bad = 0;
+    for (int level = 0; level < orc_levels(c); level++) {
+        const uint64_t *t = level ? t1 : t0;
+        int B = orc_slots_per_bucket(c, level);
+        for (uint64_t a = 0; a < c->nb[level]; a++)
+            for (int y = 0; y < B; y++) {
+                uint64_t e = orc_get_slot(c, level, t, a, y);
+                if (e == 0)
+                    continue;
+                int x;
+                uint64_t k = orc_decode(c, level, a, e, &x);
+                int ok;
+                if (c->kind == 0)
+                    ok = x >= 0 && x < c->num_hashes && orc_valid_key(c, k) &&
+                         orc_address(c, 0, x, k) == a &&
+                         orc_cuckoo_entry(c, x, k) == e;
+                else if (level == 0)
+                    ok = (e & 1) && orc_valid_key(c, k) &&
+                         orc_address(c, 0, 0, k) == a &&
+                         orc_iceberg_entry(c, 0, k) == e;
+                else
+                    ok = x >= 1 && x <= 2 && orc_valid_key(c, k) &&
+                         orc_iceberg_bucket(c, x, k) == a &&
+                         orc_iceberg_entry(c, x, k) == e;
+                if (!ok)
+                    bad++;
+            }
+    }
+    return bad;
+}
+
+/* order property: if slot (x, y) for k holds r'_x(k), every slot (x', y')
+ * preceding it holds some other key's entry (neither EMPTY nor r'_{x'}(k)) */
+uint64_t orc_check_order_property(const orc_cfg *c, const uint64_t *t0,
+                                  const uint64_t *t1)
+{
+    uint64_t bad = 0;
+    int Bx[3] = {orc_slots_per_bucket(c, 0), orc_slots_per_bucket(c, 1),
+                 orc_slots_per_bucket(c, 1)};
+    for (int level = 0; level < 2; level++) {
+        const uint64_t *t = level ? t1 : t0;
+        for (uint64_t a = 0; a < c->nb[level]; a++)
+            for (int y = 0; y < Bx[level]; y++) {
+                uint64_t e = orc_get_slot(c, level, t, a, y);
+                if (e == 0)
+                    continue;
+                int x;
+                uint64_t k = orc_decode(c, level, a, e, &x);
+                int violated = 0;
+                for (int x2 = 0; x2 < 3 && !violated; x2++)
+                    for (int y2 = 0; y2 < Bx[x2]; y2++) {
+                        if (!orc_prec(x2, y2, x, y))
+                            continue;
+                        uint64_t e2 = orc_get_slot(
+                            c, x2 ? 1 : 0, orc_level_table(x2, t0, t1),
+                            orc_iceberg_bucket(c, x2, k), y2);
+                        if (e2 == 0 || e2 == orc_iceberg_entry(c, x2, k)) {
+                            violated = 1;
+                            break;
+                        }
+                    }
+                bad += (uint64_t)violated;
+            }
+    }
+    return bad;
+}
+
+uint64_t orc_check_cuckoo_chain(const orc_cfg *c, const uint64_t *table)
+{
+    uint64_t bad = 0;
+    int B = orc_slots_per_bucket(c, 0);
+    for (uint64_t a = 0; a < c->nb[0]; a++)
+        for (int y = 0; y < B; y++) {
+            uint64_t e = orc_get_slot(c, 0, table, a, y);
+            if (e == 0)
+                continue;
+            int j;
+            uint64_t k = orc_cuckoo_decode(c, a, e, &j);
+            for (int jj = 0; jj < j; jj++)
+                if (orc_bucket_has_empty(c, 0, table, orc_address(c, 0, jj, k))) {
+                    bad++;
+                    break;
+                }
+        }
+    return bad;
+}
