@@ -1,0 +1,225 @@
+/*
+ * cht.h - C ABI of the compact parallel hash table library (GB300, sm_103a).
+ *
+ * Batched, lockless insert, find and find-or-put on compact (quotiented)
+ * bucketed hash tables, after Hegeman, Woeltgens, Wijs and Laarman, "Compact
+ * Parallel Hash Tables on the GPU". Two table kinds:
+ *
+ *   CHT_CUCKOO   bucketed cuckoo hashing with H permutations (Section 2.2,
+ *                Section 4.4, Algorithm 4): a static table, built from unique
+ *                keys and then queried.
+ *   CHT_ICEBERG  two-level iceberg hashing (Section 2.3, Section 3,
+ *                Algorithm 1): a dynamic table whose find-or-put may run
+ *                concurrently with other find-or-puts and lookups.
+ *
+ * Quotienting (Section 2.4): a permutation pi_j of the w-bit keys maps k to
+ * pi_j(k) = a . r; the first N bits a address one of 2^N buckets and only the
+ * remaining w - N bits r (plus a few tag bits) are stored, so more slots fit
+ * in one 128-byte bucket. A "whole-key" table (compact = 0) stores k itself in
+ * 64-bit slots and is the paper's non-compact baseline (Section 5.1).
+ *
+ * Conventions for every call below:
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device. The
+ *    caller owns all memory: the table storage, key arrays and outputs. The
+ *    library allocates no device memory.
+ *  - stream is a cudaStream_t passed as an opaque pointer (NULL = the legacy
+ *    default stream). Calls only enqueue work and return; results are valid
+ *    once the stream has been synchronised.
+ *  - Each call returns CHT_OK or one of the CHT_ERR_* codes; cht_last_error()
+ *    then gives a message (thread-local). Argument errors are detected on the
+ *    host before anything is enqueued. Per-key outcomes are status bytes.
+ *  - Keys are unsigned integers of key_bytes (4 or 8) bytes, little-endian,
+ *    in [1, 2^key_bits). Key 0 and keys >= 2^key_bits get status CHT_INVALID.
+ */
+#ifndef CHT_H
+#define CHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- call return codes ---- */
+#define CHT_OK 0
+#define CHT_ERR_INVALID 1     /* bad argument or configuration                */
+#define CHT_ERR_UNSUPPORTED 2 /* valid request this table kind does not offer */
+#define CHT_ERR_CUDA 3        /* a CUDA runtime call failed                   */
+#define CHT_ERR_CAPACITY 4    /* an output buffer is too small                */
+#define CHT_ERR_TIMEOUT 5     /* a bounded device wait ran out                */
+
+/* ---- per-key status bytes (Section 3: found / put / full) ---- */
+#define CHT_NOT_FOUND 0 /* lookup: key absent                                */
+#define CHT_FOUND 1     /* key present (find-or-put: it was already there)   */
+#define CHT_PUT 2       /* this call inserted the key                        */
+#define CHT_FULL 3      /* no slot available for the key                     */
+#define CHT_INVALID 4   /* key 0 or key >= 2^key_bits                        */
+#define CHT_ERROR 5     /* a bounded retry loop gave up (should not happen)  */
+
+#define CHT_CUCKOO 0
+#define CHT_ICEBERG 1
+
+/* bytes of the table header at the start of the table storage */
+#define CHT_HEADER_BYTES 256
+/* bytes per bucket: 16 words of 64 bits, one cache line (Section 4.5) */
+#define CHT_BUCKET_BYTES 128
+
+typedef struct cht_table cht_table; /* opaque host handle */
+
+/*
+ * Table configuration. Zero-valued tuning fields select defaults.
+ *
+ * kind                  CHT_CUCKOO or CHT_ICEBERG.
+ * compact               1: store remainders (quotienting, Section 2.4);
+ *                       0: store whole keys, one 64-bit slot each.
+ * key_bits              w, 2..62 (at most 32 when key_bytes = 4).
+ * key_bytes             width of the caller's key arrays: 4 or 8.
+ * num_buckets           buckets of the cuckoo table / iceberg primary level.
+ *                       A power of two when compact = 1 (Section 4.5).
+ * num_buckets_backyard  iceberg secondary-level buckets (ignored for cuckoo).
+ * fields_per_word       slots per 64-bit word of level 0, 1..4 (slot width
+ *                       64/fields_per_word bits); 0 = the densest packing in
+ *                       which every entry fits. Whole-key tables use 1.
+ * fields_per_word_backyard  the same for the iceberg secondary level.
+ * num_hashes            cuckoo H, 1..3 (0 = 3).
+ * max_chain             cuckoo C, eviction steps before a put gives up
+ *                       (Algorithm 4); 0 = 128.
+ * seed                  all permutation constants derive from it.
+ * tile                  threads cooperating on one bucket: 4, 8 or 16 (0 = 8).
+ * items_per_thread      keys each thread loads per work chunk, 1..8 (0 = 2).
+ * cta_threads           threads per block, a multiple of 32 (0 = 256).
+ * max_ctas              upper bound on blocks (0 = enough to fill the GPU).
+ * max_tiles             upper bound on tiles that take work (0 = no bound).
+ *                       With max_tiles = 1 a single tile processes the keys
+ *                       strictly in input order (a sequential run).
+ */
+typedef struct cht_config {
+    int32_t kind;
+    int32_t compact;
+    int32_t key_bits;
+    int32_t key_bytes;
+    uint64_t num_buckets;
+    uint64_t num_buckets_backyard;
+    int32_t fields_per_word;
+    int32_t fields_per_word_backyard;
+    int32_t num_hashes;
+    int32_t max_chain;
+    uint64_t seed;
+    int32_t tile;
+    int32_t items_per_thread;
+    int32_t cta_threads;
+    int32_t max_ctas;
+    int32_t max_tiles;
+    int32_t reserved[3];
+} cht_config;
+
+/* Device counters a table can accumulate into (see cht_set_counters). */
+typedef struct cht_counters {
+    uint64_t probes;     /* bucket reads (one 128-byte line each)            */
+    uint64_t writes;     /* successful slot claims and cuckoo swaps           */
+    uint64_t cas_fail;   /* claims that lost a race and were retried          */
+    uint64_t ops;        /* keys processed                                    */
+} cht_counters;
+
+/*
+ * Resolve zero fields to defaults and validate. On CHT_OK, *out holds the
+ * resolved configuration (out may alias cfg). Host only; no CUDA calls.
+ */
+int cht_resolve_config(const cht_config *cfg, cht_config *out);
+
+/*
+ * Bytes of device storage a table of this configuration needs:
+ * CHT_HEADER_BYTES + (num_buckets + num_buckets_backyard) * CHT_BUCKET_BYTES
+ * (no backyard for cuckoo). Returns 0 if the configuration is invalid.
+ * Host only.
+ */
+size_t cht_table_bytes(const cht_config *cfg);
+
+/*
+ * Create a table handle over caller-owned device storage d_mem of at least
+ * cht_table_bytes(cfg) bytes, 256-byte aligned. The storage is zeroed on
+ * stream (an empty table). The handle does not own d_mem; the caller keeps it
+ * alive until cht_destroy. *out receives the handle.
+ */
+int cht_create(const cht_config *cfg, void *d_mem, size_t bytes, void *stream,
+               cht_table **out);
+
+/* Free the host handle (the device storage stays the caller's). */
+int cht_destroy(cht_table *t);
+
+/* Empty the table again (zero its buckets and header) on stream. */
+int cht_clear(cht_table *t, void *stream);
+
+/* Copy the resolved configuration of a table into *out. Host only. */
+int cht_get_config(const cht_table *t, cht_config *out);
+
+/*
+ * Insert n keys (d_keys, key_bytes each). d_status[i] receives CHT_PUT,
+ * CHT_FULL, CHT_INVALID or (iceberg) CHT_FOUND.
+ * Cuckoo: Algorithm 4 per key. Keys must be unique within the table's
+ *   lifetime (a static build, Section 1); a put that runs out of its
+ *   max_chain eviction steps reports CHT_FULL and, when d_dropped is not
+ *   NULL, d_dropped[i] receives the key that was left without a slot (it may
+ *   be another key, evicted along the chain). d_dropped entries of keys whose
+ *   status is not CHT_FULL are not written. Must not overlap a find or
+ *   another insert on the same table.
+ * Iceberg: the same as cht_find_or_put (d_dropped is ignored).
+ */
+int cht_insert(cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
+               uint64_t *d_dropped, void *stream);
+
+/*
+ * Look up n keys. d_status[i] receives CHT_FOUND, CHT_NOT_FOUND or
+ * CHT_INVALID. Cuckoo: probes a_0, a_1, ... and stops at the first bucket
+ * that holds the key or has a free slot (Section 4.4). Iceberg: the primary
+ * bucket, then both secondary buckets if the primary is full (Section 2.3).
+ */
+int cht_find(const cht_table *t, const void *d_keys, size_t n,
+             uint8_t *d_status, void *stream);
+
+/*
+ * Iceberg find-or-put (Algorithm 1 per key): CHT_FOUND if the key was in the
+ * table, otherwise CHT_PUT if this call inserted it, or CHT_FULL if its
+ * primary and both secondary buckets are full. Duplicates within a batch and
+ * concurrent calls are allowed: of several find-or-puts of one absent key
+ * exactly one reports CHT_PUT and the others CHT_FOUND (Theorem 1).
+ * Cuckoo tables return CHT_ERR_UNSUPPORTED (Section 4.4 gives no lockless
+ * find-or-put for cuckoo hashing).
+ */
+int cht_find_or_put(cht_table *t, const void *d_keys, size_t n,
+                    uint8_t *d_status, void *stream);
+
+/*
+ * Write every stored key, decoded as k = pi_j^-1(a . r) (Section 2.4), to
+ * d_out (key_bytes each) in unspecified order, at most cap keys. *d_count (a
+ * device uint64) receives the number of stored keys, which may exceed cap;
+ * it is overwritten, not accumulated.
+ */
+int cht_enumerate(const cht_table *t, void *d_out, size_t cap,
+                  uint64_t *d_count, void *stream);
+
+/*
+ * Attach a device cht_counters block (or NULL to detach). Later calls on the
+ * table add their probe/write/retry/op counts into it with atomics. The
+ * caller zeroes it. Counting costs a few instructions per key and one atomic
+ * per warp.
+ */
+int cht_set_counters(cht_table *t, cht_counters *d_counters);
+
+/*
+ * Read the device error word of the table header (synchronises stream). A
+ * nonzero value means some key got CHT_ERROR status since the last clear.
+ */
+int cht_error_flags(const cht_table *t, uint32_t *flags, void *stream);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *cht_last_error(void);
+
+/* Library version string. */
+const char *cht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHT_H */

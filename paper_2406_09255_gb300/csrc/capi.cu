@@ -1,0 +1,351 @@
+// capi.cu - the C ABI declared in include/cht.h: configuration planning and
+// validation, table handles over caller-owned device storage, and dispatch
+// of the hot-path kernels. No device memory is allocated here.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "cht.h"
+#include "cht_kernels.cuh"
+#include "cht_scan.cuh"
+#include "cht_launch.h"
+
+using namespace cht;
+
+struct cht_table {
+    cht_config cfg;       // resolved
+    TableArgs args;       // what the kernels see
+    unsigned char *mem;   // caller's storage (header + buckets)
+    size_t bytes;
+    int device;
+    int sms;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int ok() {
+    g_err.clear();
+    return CHT_OK;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(CHT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ceil_log2(uint64_t x) {
+    int n = 0;
+    while (n < 64 && (1ull << n) < x) n++;
+    return n;
+}
+
+bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+// tag bits of an entry: cuckoo (j + 1) and iceberg secondary (i + 1) take 2,
+// the iceberg primary occupancy flag 1
+int tag_bits(int kind, int level) { return (kind == CHT_ICEBERG && level == 0) ? 1 : 2; }
+
+int resolve_level(cht_config &c, int level, uint64_t nb, int32_t &fpw) {
+    const char *lname = level ? "num_buckets_backyard" : "num_buckets";
+    if (nb < 1) return fail(CHT_ERR_INVALID, "%s must be >= 1", lname);
+    if (c.compact && !is_pow2(nb))
+        return fail(CHT_ERR_INVALID, "%s = %llu must be a power of two for a compact table",
+                    lname, (unsigned long long)nb);
+    const int n = ceil_log2(nb);
+    if (n >= c.key_bits)
+        return fail(CHT_ERR_INVALID, "%s = 2^%d leaves no remainder bits for %d-bit keys", lname,
+                    n, c.key_bits);
+    const int body = c.compact ? c.key_bits - n : c.key_bits;
+    const int need = body + tag_bits(c.kind, level);
+    if (fpw == 0) {
+        if (!c.compact) {
+            fpw = 1;
+        } else {
+            for (int f = 4; f >= 1; --f)
+                if (need <= 64 / f) {
+                    fpw = f;
+                    break;
+                }
+        }
+    }
+    if (fpw < 1 || fpw > 4)
+        return fail(CHT_ERR_INVALID, "fields per word must be 1..4 (got %d)", fpw);
+    if (need > 64 / fpw)
+        return fail(CHT_ERR_INVALID,
+                    "level %d entries need %d bits but %d fields per word give %d-bit slots",
+                    level, need, fpw, 64 / fpw);
+    return CHT_OK;
+}
+
+int resolve(const cht_config *in, cht_config *out) {
+    if (!in || !out) return fail(CHT_ERR_INVALID, "null configuration pointer");
+    cht_config c = *in;
+    if (c.kind != CHT_CUCKOO && c.kind != CHT_ICEBERG)
+        return fail(CHT_ERR_INVALID, "kind must be CHT_CUCKOO or CHT_ICEBERG");
+    if (c.compact != 0 && c.compact != 1) return fail(CHT_ERR_INVALID, "compact must be 0 or 1");
+    if (c.key_bytes != 4 && c.key_bytes != 8)
+        return fail(CHT_ERR_INVALID, "key_bytes must be 4 or 8");
+    if (c.key_bits < 2 || c.key_bits > 62 || c.key_bits > 8 * c.key_bytes)
+        return fail(CHT_ERR_INVALID, "key_bits = %d out of range for %d-byte keys", c.key_bits,
+                    c.key_bytes);
+    if (c.kind == CHT_CUCKOO) {
+        if (c.num_hashes == 0) c.num_hashes = 3;
+        if (c.num_hashes < 1 || c.num_hashes > 3)
+            return fail(CHT_ERR_INVALID, "num_hashes must be 1..3");
+        if (c.max_chain == 0) c.max_chain = 128;
+        if (c.max_chain < 1) return fail(CHT_ERR_INVALID, "max_chain must be >= 1");
+        c.num_buckets_backyard = 0;
+        c.fields_per_word_backyard = 0;
+    } else {
+        c.num_hashes = 0;
+        c.max_chain = 0;
+    }
+    int e = resolve_level(c, 0, c.num_buckets, c.fields_per_word);
+    if (e) return e;
+    if (c.kind == CHT_ICEBERG) {
+        e = resolve_level(c, 1, c.num_buckets_backyard, c.fields_per_word_backyard);
+        if (e) return e;
+    }
+    if (c.tile == 0) c.tile = 8;
+    if (c.tile != 4 && c.tile != 8 && c.tile != 16)
+        return fail(CHT_ERR_INVALID, "tile must be 4, 8 or 16 (got %d)", c.tile);
+    if (c.items_per_thread == 0) c.items_per_thread = 2;
+    if (c.items_per_thread < 1 || c.items_per_thread > 8)
+        return fail(CHT_ERR_INVALID, "items_per_thread must be 1..8");
+    if (c.cta_threads == 0) c.cta_threads = 256;
+    if (c.cta_threads < 32 || c.cta_threads > 256 || c.cta_threads % 32)
+        return fail(CHT_ERR_INVALID, "cta_threads must be a multiple of 32 in [32, 256]");
+    if (c.max_ctas < 0 || c.max_tiles < 0)
+        return fail(CHT_ERR_INVALID, "max_ctas and max_tiles must be >= 0");
+    *out = c;
+    return CHT_OK;
+}
+
+size_t table_bytes(const cht_config &c) {
+    uint64_t nb = c.num_buckets + (c.kind == CHT_ICEBERG ? c.num_buckets_backyard : 0);
+    return CHT_HEADER_BYTES + (size_t)nb * CHT_BUCKET_BYTES;
+}
+
+void fill_level(Level &L, uint64_t *words, uint64_t nb, int key_bits, int fpw, uint64_t seed,
+                int level) {
+    L.words = words;
+    L.nb = nb;
+    L.n = ceil_log2(nb);
+    L.R = key_bits - L.n;
+    L.pow2 = is_pow2(nb);
+    L.fpw = fpw;
+    for (int j = 0; j < 3; ++j) {
+        const uint64_t idx = 2ull * (uint64_t)(4 * level + j);
+        L.A[j] = splitmix(seed, idx) | 1ull;
+        L.B[j] = splitmix(seed, idx + 1);
+    }
+}
+
+LaunchParams launch_params(const cht_table *t, void *stream) {
+    LaunchParams lp;
+    lp.cta = t->cfg.cta_threads;
+    lp.items = t->cfg.items_per_thread;
+    lp.max_ctas = t->cfg.max_ctas;
+    lp.max_tiles = t->cfg.max_tiles;
+    lp.sms = t->sms;
+    lp.stream = static_cast<cudaStream_t>(stream);
+    return lp;
+}
+
+int check_keys(const cht_table *t, const void *d_keys, size_t n, const void *d_out) {
+    if (!t) return fail(CHT_ERR_INVALID, "null table");
+    if (n && (!d_keys || !d_out)) return fail(CHT_ERR_INVALID, "null key or output pointer");
+    if ((uintptr_t)d_keys % t->cfg.key_bytes)
+        return fail(CHT_ERR_INVALID, "key array not aligned to %d bytes", t->cfg.key_bytes);
+    return CHT_OK;
+}
+
+int clear_storage(cht_table *t, cudaStream_t s) {
+    const uint64_t n16 = t->bytes / 16;
+    int blocks = (int)std::min<uint64_t>((n16 + 255) / 256, (uint64_t)t->sms * 8);
+    if (blocks < 1) blocks = 1;
+    k_clear<<<blocks, 256, 0, s>>>(reinterpret_cast<ulonglong2 *>(t->mem), n16);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CHT_OK : cuda_fail(e, "clear kernel launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+int cht_resolve_config(const cht_config *cfg, cht_config *out) {
+    int e = resolve(cfg, out);
+    return e ? e : ok();
+}
+
+size_t cht_table_bytes(const cht_config *cfg) {
+    cht_config c;
+    if (resolve(cfg, &c)) return 0;
+    return table_bytes(c);
+}
+
+int cht_create(const cht_config *cfg, void *d_mem, size_t bytes, void *stream, cht_table **out) {
+    if (!out) return fail(CHT_ERR_INVALID, "null output handle pointer");
+    *out = nullptr;
+    cht_config c;
+    int e = resolve(cfg, &c);
+    if (e) return e;
+    const size_t need = table_bytes(c);
+    if (!d_mem) return fail(CHT_ERR_INVALID, "null table storage");
+    if ((uintptr_t)d_mem % 256) return fail(CHT_ERR_INVALID, "table storage not 256-byte aligned");
+    if (bytes < need)
+        return fail(CHT_ERR_CAPACITY, "table storage of %zu bytes is below the %zu needed", bytes,
+                    need);
+    cht_table *t = new cht_table();
+    t->cfg = c;
+    t->mem = static_cast<unsigned char *>(d_mem);
+    t->bytes = need;
+    cudaError_t ce = cudaGetDevice(&t->device);
+    if (ce == cudaSuccess)
+        ce = cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device);
+    if (ce != cudaSuccess) {
+        delete t;
+        return cuda_fail(ce, "device query");
+    }
+    TableArgs &a = t->args;
+    memset(&a, 0, sizeof a);
+    uint64_t *words0 = reinterpret_cast<uint64_t *>(t->mem + CHT_HEADER_BYTES);
+    fill_level(a.lv[0], words0, c.num_buckets, c.key_bits, c.fields_per_word, c.seed, 0);
+    if (c.kind == CHT_ICEBERG)
+        fill_level(a.lv[1], words0 + c.num_buckets * kWordsPerBucket, c.num_buckets_backyard,
+                   c.key_bits, c.fields_per_word_backyard, c.seed, 1);
+    a.w = c.key_bits;
+    a.key_bytes = c.key_bytes;
+    a.H = c.num_hashes;
+    a.C = c.max_chain;
+    a.compact = c.compact;
+    a.max_tiles = c.max_tiles;
+    a.err = reinterpret_cast<uint32_t *>(t->mem);
+    a.ctr = nullptr;
+    e = clear_storage(t, static_cast<cudaStream_t>(stream));
+    if (e) {
+        delete t;
+        return e;
+    }
+    *out = t;
+    return ok();
+}
+
+int cht_destroy(cht_table *t) {
+    delete t;
+    return ok();
+}
+
+int cht_clear(cht_table *t, void *stream) {
+    if (!t) return fail(CHT_ERR_INVALID, "null table");
+    int e = clear_storage(t, static_cast<cudaStream_t>(stream));
+    return e ? e : ok();
+}
+
+int cht_get_config(const cht_table *t, cht_config *out) {
+    if (!t || !out) return fail(CHT_ERR_INVALID, "null argument");
+    *out = t->cfg;
+    return ok();
+}
+
+int cht_insert(cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
+               uint64_t *d_dropped, void *stream) {
+    int e = check_keys(t, d_keys, n, d_status);
+    if (e) return e;
+    if (n == 0) return ok();
+    const LaunchParams lp = launch_params(t, stream);
+    cudaError_t ce;
+    if (t->cfg.kind == CHT_CUCKOO)
+        ce = launch_cuckoo_insert(t->cfg.tile, t->cfg.fields_per_word, lp, t->args, d_keys, n,
+                                  d_status, d_dropped);
+    else
+        ce = launch_iceberg(t->cfg.tile, t->cfg.fields_per_word, false, lp, t->args, d_keys, n,
+                            d_status);
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "insert kernel launch");
+}
+
+int cht_find(const cht_table *t, const void *d_keys, size_t n, uint8_t *d_status, void *stream) {
+    int e = check_keys(t, d_keys, n, d_status);
+    if (e) return e;
+    if (n == 0) return ok();
+    const LaunchParams lp = launch_params(t, stream);
+    cudaError_t ce;
+    if (t->cfg.kind == CHT_CUCKOO)
+        ce = launch_cuckoo_find(t->cfg.tile, t->cfg.fields_per_word, lp, t->args, d_keys, n,
+                                d_status);
+    else
+        ce = launch_iceberg(t->cfg.tile, t->cfg.fields_per_word, true, lp, t->args, d_keys, n,
+                            d_status);
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "find kernel launch");
+}
+
+int cht_find_or_put(cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
+                    void *stream) {
+    int e = check_keys(t, d_keys, n, d_status);
+    if (e) return e;
+    if (t->cfg.kind != CHT_ICEBERG)
+        return fail(CHT_ERR_UNSUPPORTED,
+                    "find-or-put is offered by iceberg tables only (cuckoo tables are static)");
+    if (n == 0) return ok();
+    const LaunchParams lp = launch_params(t, stream);
+    cudaError_t ce = launch_iceberg(t->cfg.tile, t->cfg.fields_per_word, false, lp, t->args,
+                                    d_keys, n, d_status);
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "find-or-put kernel launch");
+}
+
+int cht_enumerate(const cht_table *t, void *d_out, size_t cap, uint64_t *d_count, void *stream) {
+    if (!t) return fail(CHT_ERR_INVALID, "null table");
+    if (!d_count) return fail(CHT_ERR_INVALID, "null count pointer");
+    if (cap && !d_out) return fail(CHT_ERR_INVALID, "null output with nonzero capacity");
+    if ((uintptr_t)d_out % t->cfg.key_bytes)
+        return fail(CHT_ERR_INVALID, "output not aligned to %d bytes", t->cfg.key_bytes);
+    if ((uintptr_t)d_count % 8) return fail(CHT_ERR_INVALID, "count not 8-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto *cnt = reinterpret_cast<unsigned long long *>(d_count);
+    k_zero_u64<<<1, 32, 0, s>>>(cnt);
+    const uint64_t words = (t->cfg.num_buckets +
+                            (t->cfg.kind == CHT_ICEBERG ? t->cfg.num_buckets_backyard : 0)) *
+                           kWordsPerBucket;
+    uint64_t blocks = (words / 2 + 255) / 256;
+    const uint64_t cap_blocks = (uint64_t)t->sms * 8;
+    if (blocks > cap_blocks) blocks = cap_blocks;
+    if (blocks < 1) blocks = 1;
+    k_enumerate<<<(int)blocks, 256, 0, s>>>(t->args, t->cfg.kind, d_out, cap, cnt);
+    cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "enumerate kernel launch");
+}
+
+int cht_set_counters(cht_table *t, cht_counters *d_counters) {
+    if (!t) return fail(CHT_ERR_INVALID, "null table");
+    if ((uintptr_t)d_counters % 8) return fail(CHT_ERR_INVALID, "counters not 8-byte aligned");
+    t->args.ctr = reinterpret_cast<unsigned long long *>(d_counters);
+    return ok();
+}
+
+int cht_error_flags(const cht_table *t, uint32_t *flags, void *stream) {
+    if (!t || !flags) return fail(CHT_ERR_INVALID, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t ce = cudaMemcpyAsync(flags, t->args.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "reading the error word");
+}
+
+const char *cht_last_error(void) { return g_err.c_str(); }
+
+const char *cht_version(void) { return "cht 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,395 @@
+// cht_device.cuh - device-side building blocks of the compact hash tables:
+// the quotienting permutation (Section 2.4, Section 4.3), the packed bucket
+// layout, cooperative-tile primitives (Section 4.1: Any / Count / First /
+// Shuffle over a tile of T threads that owns one bucket) and the field-level
+// compare-and-swap and swap used by Algorithms 1 and 4.
+//
+// Bucket layout: a bucket is 16 little-endian 64-bit words (128 bytes, one
+// cache line, Section 4.5). A level stores fpw fields per word, each
+// S = 64 / fpw bits wide; slot y is field y % fpw of word y / fpw. The
+// all-zero field is EMPTY. Entries:
+//   cuckoo            (body << 2) | (j + 1)   j = hash index (Section 2.2)
+//   iceberg primary   (body << 1) | 1         one occupancy bit (Section 5.1)
+//   iceberg secondary (body << 2) | (i + 1)   i = secondary choice (Algorithm 1)
+// where body is the remainder r_j(k) for compact tables and k itself for
+// whole-key tables.
+//
+// In a tile of T threads lane l owns words [l * W, l * W + W), W = 16 / T,
+// i.e. slots [l * W * fpw, (l + 1) * W * fpw): slot order runs lane by lane,
+// so "the first empty slot" is found with one ballot plus a local scan.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cht {
+
+constexpr int kWordsPerBucket = 16;
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+// status bytes (mirror include/cht.h)
+constexpr uint8_t ST_NOT_FOUND = 0, ST_FOUND = 1, ST_PUT = 2, ST_FULL = 3,
+                  ST_INVALID = 4, ST_ERROR = 5;
+
+// One level of a table (cuckoo table, iceberg primary or iceberg secondary).
+struct Level {
+    uint64_t *words;  // bucket b starts at words + 16 * b
+    uint64_t nb;      // bucket count
+    int n;            // address bits, ceil(log2 nb)
+    int R;            // remainder bits, w - n
+    int pow2;         // nb == 2^n
+    int fpw;          // fields per word (also a template parameter)
+    uint64_t A[3];    // Feistel round-function multipliers (odd), per hash
+    uint64_t B[3];    // Feistel round-function offsets, per hash
+};
+
+// Everything a kernel needs about a table, passed by value.
+struct TableArgs {
+    Level lv[2];
+    int w;                    // key bits
+    int key_bytes;            // 4 or 8
+    int H;                    // cuckoo hash count
+    int C;                    // cuckoo chain bound
+    int compact;              // 1: remainders, 0: whole keys
+    int max_tiles;            // 0 = unbounded
+    uint32_t *err;            // header error word
+    unsigned long long *ctr;  // optional cht_counters (probes, writes, cas_fail, ops)
+};
+
+// ---------------------------------------------------------------------------
+// splitmix64 (Steele, Lea and Flood 2014)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t splitmix(uint64_t s, uint64_t idx) {
+    return mix64(s + (idx + 1) * kGamma);
+}
+
+// ---------------------------------------------------------------------------
+// Permutation pi_j and quotient (Section 2.4). One-round Feistel: the low R
+// bits r of k pass through, the high n bits are XORed with f_j(r), a
+// multiply-shift hash of r. a = the high n bits of pi_j(k), remainder = r.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t round_fn(const Level &L, int j, uint64_t r) {
+    return L.n ? (L.A[j] * r + L.B[j]) >> (64 - L.n) : 0ull;
+}
+
+__device__ __forceinline__ uint64_t low_mask(int bits) {
+    return bits >= 64 ? ~0ull : ((1ull << bits) - 1ull);
+}
+
+struct Quot {
+    uint64_t a;  // bucket address
+    uint64_t r;  // remainder
+};
+
+__device__ __forceinline__ Quot quotient(const Level &L, int w, int j, uint64_t k) {
+    uint64_t r = k & low_mask(L.R);
+    uint64_t hi = (k >> L.R) ^ round_fn(L, j, r);
+    if (L.pow2) return {hi, r};
+    // bucket count not a power of two (whole-key tables): scale pi_j(k) onto [0, nb)
+    uint64_t p = (hi << L.R) | r;
+    uint64_t lo = p * L.nb, h = __umul64hi(p, L.nb);
+    return {(h << (64 - w)) | (lo >> w), r};
+}
+
+// k = pi_j^-1(a . r)
+__device__ __forceinline__ uint64_t unquotient(const Level &L, int j, uint64_t a, uint64_t r) {
+    return ((a ^ round_fn(L, j, r)) << L.R) | r;
+}
+
+// ---------------------------------------------------------------------------
+// Fields
+// ---------------------------------------------------------------------------
+template <int FPW>
+struct Fields {
+    static constexpr int S = 64 / FPW;
+    static constexpr uint64_t M = (S >= 64) ? ~0ull : ((1ull << S) - 1ull);
+    __device__ __forceinline__ static uint64_t get(uint64_t word, int f) {
+        return (word >> (f * S)) & M;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Bucket chunk loads. Concurrent writers exist during insert / find-or-put,
+// so those loads are relaxed at GPU scope (each 64-bit element single-copy
+// atomic; a snapshot may be torn across words, which the algorithms
+// tolerate: a stale EMPTY only makes a later CAS fail). Static lookups use
+// the read-only path.
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ void load_relaxed(const uint64_t *p, uint64_t (&v)[W]) {
+    if constexpr (W == 1) {
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v[0]) : "l"(p) : "memory");
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2)
+            asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];"
+                         : "=l"(v[i]), "=l"(v[i + 1])
+                         : "l"(p + i)
+                         : "memory");
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void load_readonly(const uint64_t *p, uint64_t (&v)[W]) {
+    if constexpr (W == 1) {
+        v[0] = __ldg(reinterpret_cast<const unsigned long long *>(p));
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2) {
+            ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2 *>(p + i));
+            v[i] = x.x;
+            v[i + 1] = x.y;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile primitives. A tile is T consecutive lanes of a warp; every lane of the
+// warp executes these together (full-warp masks), each tile reading its own
+// bits.
+// ---------------------------------------------------------------------------
+template <int T>
+__device__ __forceinline__ uint32_t tile_bits(uint32_t warp_ballot) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t m = (T == 32) ? 0xffffffffu : ((1u << T) - 1u);
+    return (warp_ballot >> (lane & ~(T - 1))) & m;
+}
+template <int T>
+__device__ __forceinline__ uint32_t tile_ballot(bool p) {
+    return tile_bits<T>(__ballot_sync(0xffffffffu, p));
+}
+// value of v held by tile lane src (src relative to the tile)
+template <int T, typename V>
+__device__ __forceinline__ V tile_shfl(V v, int src) {
+    return __shfl_sync(0xffffffffu, v, src, T);
+}
+template <int T>
+__device__ __forceinline__ bool tile_shfl(bool v, int src) {
+    return __shfl_sync(0xffffffffu, (int)v, src, T) != 0;
+}
+
+// per-lane scan of the owned fields: whether one equals `entry`, and the local
+// index of the first EMPTY field (-1 if none)
+template <int W, int FPW>
+__device__ __forceinline__ void scan_chunk(const uint64_t (&v)[W], uint64_t entry, bool &match,
+                                           int &first_empty) {
+    match = false;
+    first_empty = -1;
+#pragma unroll
+    for (int i = W - 1; i >= 0; --i) {
+#pragma unroll
+        for (int f = FPW - 1; f >= 0; --f) {
+            uint64_t x = Fields<FPW>::get(v[i], f);
+            match |= (x == entry);
+            if (x == 0) first_empty = i * FPW + f;
+        }
+    }
+}
+
+// the same with the packing known only at run time (fpw in 1..4)
+template <int W>
+__device__ __forceinline__ void scan_chunk_rt(const uint64_t (&v)[W], uint64_t entry, int fpw,
+                                              bool &match, int &first_empty) {
+    const int S = 64 / fpw;
+    const uint64_t M = (S >= 64) ? ~0ull : ((1ull << S) - 1ull);
+    match = false;
+    first_empty = -1;
+#pragma unroll
+    for (int i = W - 1; i >= 0; --i) {
+#pragma unroll
+        for (int f = 3; f >= 0; --f) {
+            if (f < fpw) {
+                uint64_t x = (v[i] >> (f * S)) & M;
+                match |= (x == entry);
+                if (x == 0) first_empty = i * fpw + f;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Field-level compare-and-swap EMPTY -> entry on field f of *wp, emulated on
+// the narrowest naturally aligned atomic that contains the field: 16-bit and
+// 32-bit fields use native sub-word CAS, 21-bit fields a 64-bit CAS that is
+// retried while only neighbouring fields changed (fields only ever go from
+// EMPTY to filled, so the retry count is bounded by the fields per word).
+// Returns true if this thread wrote the entry; otherwise *seen holds the
+// field value that won.
+// ---------------------------------------------------------------------------
+template <int FPW>
+__device__ __forceinline__ bool claim_field(uint64_t *wp, int f, uint64_t snap_word,
+                                            uint64_t entry, uint64_t &seen, int &fails) {
+    using F = Fields<FPW>;
+    if constexpr (FPW == 1) {
+        unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long *>(wp), 0ull,
+                                           static_cast<unsigned long long>(entry));
+        seen = old;
+        if (old != 0ull) fails++;
+        return old == 0ull;
+    } else if constexpr (FPW == 2) {
+        unsigned int *hp = reinterpret_cast<unsigned int *>(wp) + f;
+        unsigned int old = atomicCAS(hp, 0u, static_cast<unsigned int>(entry));
+        seen = old;
+        if (old != 0u) fails++;
+        return old == 0u;
+    } else if constexpr (FPW == 4) {
+        unsigned short *hp = reinterpret_cast<unsigned short *>(wp) + f;
+        unsigned short old = atomicCAS(hp, static_cast<unsigned short>(0),
+                                       static_cast<unsigned short>(entry));
+        seen = old;
+        if (old != 0) fails++;
+        return old == 0;
+    } else {
+        uint64_t expected = snap_word & ~(F::M << (f * F::S));
+        for (int it = 0; it < 64; ++it) {
+            uint64_t desired = expected | (entry << (f * F::S));
+            unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long *>(wp),
+                                               expected, desired);
+            if (old == expected) return true;
+            fails++;
+            uint64_t fld = F::get(old, f);
+            if (fld != 0) {
+                seen = fld;
+                return false;
+            }
+            expected = old;
+        }
+        seen = 0;  // gave up on this word; the caller re-reads the bucket
+        return false;
+    }
+}
+
+__device__ __forceinline__ bool claim_field_rt(int fpw, uint64_t *wp, int f, uint64_t snap_word,
+                                               uint64_t entry, uint64_t &seen, int &fails);
+
+// Atomic swap of field f of *wp with `entry` (Algorithm 4's Swap). Returns the
+// previous field value; sets ok = false if a bounded retry loop gave up.
+template <int FPW>
+__device__ __forceinline__ uint64_t swap_field(uint64_t *wp, int f, uint64_t snap_word,
+                                               uint64_t entry, bool &ok) {
+    using F = Fields<FPW>;
+    ok = true;
+    if constexpr (FPW == 1) {
+        return atomicExch(reinterpret_cast<unsigned long long *>(wp),
+                          static_cast<unsigned long long>(entry));
+    } else if constexpr (FPW == 2) {
+        return atomicExch(reinterpret_cast<unsigned int *>(wp) + f,
+                          static_cast<unsigned int>(entry));
+    } else {
+        uint64_t expected = snap_word;
+        for (int it = 0; it < 4096; ++it) {
+            uint64_t desired = (expected & ~(F::M << (f * F::S))) | (entry << (f * F::S));
+            unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long *>(wp),
+                                               expected, desired);
+            if (old == expected) return F::get(old, f);
+            expected = old;
+        }
+        ok = false;
+        return 0;
+    }
+}
+
+__device__ __forceinline__ bool claim_field_rt(int fpw, uint64_t *wp, int f, uint64_t snap_word,
+                                               uint64_t entry, uint64_t &seen, int &fails) {
+    switch (fpw) {
+        case 1: return claim_field<1>(wp, f, snap_word, entry, seen, fails);
+        case 2: return claim_field<2>(wp, f, snap_word, entry, seen, fails);
+        case 3: return claim_field<3>(wp, f, snap_word, entry, seen, fails);
+        default: return claim_field<4>(wp, f, snap_word, entry, seen, fails);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Keys
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t load_key(const void *keys, int key_bytes, uint64_t i) {
+    if (key_bytes == 8) return __ldg(static_cast<const unsigned long long *>(keys) + i);
+    return __ldg(static_cast<const unsigned int *>(keys) + i);
+}
+__device__ __forceinline__ void store_key(void *out, int key_bytes, uint64_t i, uint64_t k) {
+    if (key_bytes == 8)
+        static_cast<unsigned long long *>(out)[i] = k;
+    else
+        static_cast<unsigned int *>(out)[i] = static_cast<unsigned int>(k);
+}
+__device__ __forceinline__ bool valid_key(uint64_t k, int w) {
+    return k != 0 && (k >> w) == 0;
+}
+
+// add a per-thread counter into the table's counters, one atomic per warp
+__device__ __forceinline__ void flush_counter(unsigned long long *ctr, int idx, uint64_t v) {
+    unsigned long long s = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr + idx, s);
+}
+
+// ---------------------------------------------------------------------------
+// Work distribution (Algorithm 3, cooperative work sharing). Each tile takes
+// chunks of T * items consecutive keys, stages them in shared memory and
+// processes them one at a time in input order; statuses are staged too and
+// written back per chunk. The per-tile state machine advances every tile of a
+// warp in lock step so that ballots and shuffles see full warps.
+// ---------------------------------------------------------------------------
+template <int T>
+struct TileWork {
+    uint64_t *s_keys;  // T * items keys of this tile
+    uint8_t *s_st;     // T * items status bytes
+    uint64_t chunk, nchunks, stride;
+    uint64_t base;
+    int q, qn, items;
+    bool done;
+
+    __device__ __forceinline__ void init(uint64_t *smem_keys, uint8_t *smem_st, int items_,
+                                         uint64_t n, int max_tiles) {
+        const int tiles_per_block = blockDim.x / T;
+        const int tib = threadIdx.x / T;
+        items = items_;
+        s_keys = smem_keys + (size_t)tib * T * items;
+        s_st = smem_st + (size_t)tib * T * items;
+        const uint64_t tile_id = (uint64_t)blockIdx.x * tiles_per_block + tib;
+        uint64_t ntiles = (uint64_t)gridDim.x * tiles_per_block;
+        if (max_tiles > 0 && ntiles > (uint64_t)max_tiles) ntiles = max_tiles;
+        const uint64_t per = (uint64_t)T * items;
+        nchunks = (n + per - 1) / per;
+        stride = ntiles;
+        chunk = tile_id;
+        done = (tile_id >= ntiles) || (chunk >= nchunks);
+        q = qn = 0;
+        base = 0;
+    }
+
+    // stage the next chunk's keys (called with q >= qn by every lane of the tile)
+    __device__ __forceinline__ void refill(const void *keys, int key_bytes, uint64_t n,
+                                           uint8_t *status) {
+        const int tl = threadIdx.x & (T - 1);
+        const uint64_t per = (uint64_t)T * items;
+        if (qn > 0) {
+            for (int i = 0; i < items; ++i) {
+                int idx = i * T + tl;
+                if (idx < qn) status[base + idx] = s_st[idx];
+            }
+            chunk += stride;
+        }
+        if (chunk >= nchunks) {
+            done = true;
+            qn = q = 0;
+            return;
+        }
+        base = chunk * per;
+        uint64_t rem = n - base;
+        qn = rem < per ? (int)rem : (int)per;
+        q = 0;
+        for (int i = 0; i < items; ++i) {
+            int idx = i * T + tl;
+            if (idx < qn) s_keys[idx] = load_key(keys, key_bytes, base + idx);
+        }
+    }
+};
+
+}  // namespace cht

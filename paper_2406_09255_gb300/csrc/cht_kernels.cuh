@@ -1,0 +1,393 @@
+// cht_kernels.cuh - the hot-path kernels, templated on the tile width T
+// (threads per bucket) and the packing FPW (fields per 64-bit word).
+//
+// Every kernel is persistent: tiles loop over chunks of keys (TileWork), and
+// each loop iteration performs at most one bucket probe step per tile. All
+// lanes of a warp run the loop body together; what differs between tiles is
+// carried in predicates, so every ballot and shuffle is a full-warp one.
+#pragma once
+
+#include "cht_device.cuh"
+
+namespace cht {
+
+template <int W>
+__device__ __forceinline__ uint64_t pick_word(const uint64_t (&v)[W], int i) {
+    uint64_t r = v[0];
+#pragma unroll
+    for (int k = 1; k < W; ++k)
+        if (i == k) r = v[k];
+    return r;
+}
+
+// shared memory bytes per block: keys (8 B) and status (1 B) per staged key
+__host__ __device__ inline size_t smem_bytes(int cta_threads, int items) {
+    return (size_t)cta_threads * items * 9;
+}
+
+// ===========================================================================
+// Compact cuckoo put, Algorithm 4. Per key: probe a_j(k); if the bucket has
+// an empty slot, CAS the first one; otherwise swap (r, j) into the slot chosen
+// from (k, c) and continue with the evicted key under hash (j' + 1) mod H. A
+// failed CAS also consumes a step. After C steps the put reports FULL and the
+// key in hand is the dropped one.
+// ===========================================================================
+template <int T, int FPW>
+__global__ void __launch_bounds__(256)
+    k_cuckoo_insert(TableArgs ta, const void *__restrict__ keys, uint64_t n,
+                    uint8_t *__restrict__ status, uint64_t *__restrict__ dropped, int items) {
+    constexpr int W = kWordsPerBucket / T;
+    constexpr int LF = W * FPW;  // fields per lane
+    constexpr int B = kWordsPerBucket * FPW;
+    extern __shared__ uint64_t smem[];
+    TileWork<T> tw;
+    tw.init(smem, reinterpret_cast<uint8_t *>(smem + (size_t)blockDim.x * items), items, n,
+            ta.max_tiles);
+    const int tl = threadIdx.x & (T - 1);
+    const Level &L = ta.lv[0];
+    uint64_t cur = 0;
+    int j = 0, c = 0;
+    bool fresh = true;
+    uint64_t n_probe = 0, n_write = 0, n_ops = 0;
+    int n_fail = 0;
+
+    while (__any_sync(0xffffffffu, !tw.done)) {
+        if (!tw.done && tw.q >= tw.qn) tw.refill(keys, ta.key_bytes, n, status);
+        __syncwarp();
+        const bool act = !tw.done;
+        if (act && fresh) {
+            cur = tw.s_keys[tw.q];
+            j = 0;
+            c = 1;
+            fresh = false;
+        }
+        const bool inval = act && !valid_key(cur, ta.w);
+        const bool probe = act && !inval;
+
+        const Quot qt = quotient(L, ta.w, j, cur);
+        const uint64_t entry = ((ta.compact ? qt.r : cur) << 2) | (uint64_t)(j + 1);
+        uint64_t *bp = L.words + qt.a * kWordsPerBucket + tl * W;
+        uint64_t v[W] = {};
+        if (probe) load_relaxed<W>(bp, v);
+        bool m;
+        int fe;
+        scan_chunk<W, FPW>(v, entry, m, fe);
+        const uint32_t be = tile_ballot<T>(probe && fe >= 0);
+        const int cl = be ? __ffs(be) - 1 : 0;
+        // slot to evict if the bucket is full: "pseudorandomly, based on c, k"
+        const int y = (int)(((splitmix(cur, (uint64_t)c) >> 32) * (uint64_t)B) >> 32);
+        const int el = y / LF, ef = y - el * LF;
+
+        bool claimed = false, swap_ok = true;
+        uint64_t seen = 0, evicted = 0;
+        if (probe && be && tl == cl)
+            claimed = claim_field<FPW>(bp + fe / FPW, fe % FPW, pick_word<W>(v, fe / FPW), entry,
+                                       seen, n_fail);
+        if (probe && !be && tl == el)
+            evicted = swap_field<FPW>(bp + ef / FPW, ef % FPW, pick_word<W>(v, ef / FPW), entry,
+                                      swap_ok);
+        claimed = tile_shfl<T>(claimed, cl);
+        evicted = tile_shfl<T>(evicted, el);
+        swap_ok = tile_shfl<T>(swap_ok, el);
+
+        if (act) {
+            bool fin = false;
+            uint8_t st = ST_PUT;
+            if (inval) {
+                fin = true;
+                st = ST_INVALID;
+            } else {
+                n_probe++;
+                if (be) {
+                    if (claimed) {
+                        fin = true;
+                        n_write++;
+                    } else if (++c > ta.C) {
+                        fin = true;
+                        st = ST_FULL;
+                    }
+                } else if (!swap_ok) {
+                    fin = true;
+                    st = ST_ERROR;
+                } else {
+                    n_write++;
+                    if (evicted == 0) {
+                        fin = true;  // the chosen slot held nothing: placed
+                    } else {
+                        const int jo = (int)(evicted & 3) - 1;
+                        cur = ta.compact ? unquotient(L, jo, qt.a, evicted >> 2) : (evicted >> 2);
+                        j = (jo + 1 == ta.H) ? 0 : jo + 1;
+                        if (++c > ta.C) {
+                            fin = true;
+                            st = ST_FULL;
+                        }
+                    }
+                }
+            }
+            if (fin) {
+                if (tl == 0) {
+                    tw.s_st[tw.q] = st;
+                    if (st == ST_FULL && dropped) dropped[tw.base + tw.q] = cur;
+                    if (st == ST_ERROR) atomicOr(ta.err, 1u);
+                    n_ops++;
+                }
+                tw.q++;
+                fresh = true;
+            }
+        }
+        __syncwarp();
+    }
+    if (ta.ctr) {
+        if (tl != 0) n_probe = n_write = 0;
+        flush_counter(ta.ctr, 0, n_probe);
+        flush_counter(ta.ctr, 1, n_write);
+        flush_counter(ta.ctr, 2, (uint64_t)n_fail);
+        flush_counter(ta.ctr, 3, n_ops);
+    }
+}
+
+// ===========================================================================
+// Compact cuckoo lookup, Section 4.4: probe a_0, a_1, ... for (r_j, j); stop
+// at the first bucket that holds it (FOUND) or that is not full (NOT_FOUND).
+// The table is not written while a lookup runs (static table), so buckets
+// are read through the read-only path.
+// ===========================================================================
+template <int T, int FPW>
+__global__ void __launch_bounds__(256)
+    k_cuckoo_find(TableArgs ta, const void *__restrict__ keys, uint64_t n,
+                  uint8_t *__restrict__ status, int items) {
+    constexpr int W = kWordsPerBucket / T;
+    extern __shared__ uint64_t smem[];
+    TileWork<T> tw;
+    tw.init(smem, reinterpret_cast<uint8_t *>(smem + (size_t)blockDim.x * items), items, n,
+            ta.max_tiles);
+    const int tl = threadIdx.x & (T - 1);
+    const Level &L = ta.lv[0];
+    uint64_t cur = 0;
+    int j = 0;
+    bool fresh = true;
+    uint64_t n_probe = 0, n_ops = 0;
+
+    while (__any_sync(0xffffffffu, !tw.done)) {
+        if (!tw.done && tw.q >= tw.qn) tw.refill(keys, ta.key_bytes, n, status);
+        __syncwarp();
+        const bool act = !tw.done;
+        if (act && fresh) {
+            cur = tw.s_keys[tw.q];
+            j = 0;
+            fresh = false;
+        }
+        const bool inval = act && !valid_key(cur, ta.w);
+        const bool probe = act && !inval;
+        const Quot qt = quotient(L, ta.w, j, cur);
+        const uint64_t entry = ((ta.compact ? qt.r : cur) << 2) | (uint64_t)(j + 1);
+        uint64_t v[W] = {};
+        if (probe) load_readonly<W>(L.words + qt.a * kWordsPerBucket + tl * W, v);
+        bool m;
+        int fe;
+        scan_chunk<W, FPW>(v, entry, m, fe);
+        const uint32_t bm = tile_ballot<T>(probe && m);
+        const uint32_t be = tile_ballot<T>(probe && fe >= 0);
+        if (act) {
+            bool fin = true;
+            uint8_t st = ST_NOT_FOUND;
+            if (inval) {
+                st = ST_INVALID;
+            } else {
+                n_probe++;
+                if (bm)
+                    st = ST_FOUND;
+                else if (!be && j + 1 < ta.H) {
+                    fin = false;
+                    j++;
+                }
+            }
+            if (fin) {
+                if (tl == 0) {
+                    tw.s_st[tw.q] = st;
+                    n_ops++;
+                }
+                tw.q++;
+                fresh = true;
+            }
+        }
+        __syncwarp();
+    }
+    if (ta.ctr) {
+        if (tl != 0) n_probe = 0;
+        flush_counter(ta.ctr, 0, n_probe);
+        flush_counter(ta.ctr, 3, n_ops);
+    }
+}
+
+// ===========================================================================
+// Compact iceberg find-or-put, Algorithm 1 (cooperative form of Algorithm 2).
+// Level 1: snapshot the primary bucket; FOUND if it holds r_0(k); if it has
+// an empty slot CAS the first one (PUT, or re-inspect the value that won);
+// if it is full go to level 2. Level 2: snapshot both secondary buckets;
+// FOUND if either holds (r_i(k), i - 1); otherwise pick the one whose first
+// empty slot comes first in the slot order of Definition 1 (the strictly less
+// full one, ties to the second), FULL if it has none, else CAS its first
+// empty slot. A failed CAS re-inspects the winning value and, unless it is
+// k's own entry, re-reads the buckets; the termination lemma of Appendix A
+// bounds the retries by the slots involved.
+// When lookup_only is set the kernel is the Section 2.3 lookup instead.
+// ===========================================================================
+// The primary packing FPW0 is a template parameter; the secondary level,
+// visited only by keys whose primary bucket is full, reads its packing at
+// run time.
+template <int T, int FPW0, bool LOOKUP>
+__global__ void __launch_bounds__(256)
+    k_iceberg(TableArgs ta, const void *__restrict__ keys, uint64_t n,
+              uint8_t *__restrict__ status, int items) {
+    constexpr int W = kWordsPerBucket / T;
+    const int FPW1 = ta.lv[1].fpw;
+    const int LF1 = W * FPW1;
+    const int B1 = kWordsPerBucket * FPW1;
+    const int kMaxIter = 4 * (kWordsPerBucket * FPW0 + 2 * B1) + 16;
+    extern __shared__ uint64_t smem[];
+    TileWork<T> tw;
+    tw.init(smem, reinterpret_cast<uint8_t *>(smem + (size_t)blockDim.x * items), items, n,
+            ta.max_tiles);
+    const int tl = threadIdx.x & (T - 1);
+    const Level &L0 = ta.lv[0];
+    const Level &L1 = ta.lv[1];
+    uint64_t cur = 0;
+    int lvl = 1, it = 0;
+    bool fresh = true;
+    uint64_t n_probe = 0, n_write = 0, n_ops = 0;
+    int n_fail = 0;
+
+    while (__any_sync(0xffffffffu, !tw.done)) {
+        if (!tw.done && tw.q >= tw.qn) tw.refill(keys, ta.key_bytes, n, status);
+        __syncwarp();
+        const bool act = !tw.done;
+        if (act && fresh) {
+            cur = tw.s_keys[tw.q];
+            lvl = 1;
+            it = 0;
+            fresh = false;
+        }
+        const bool inval = act && !valid_key(cur, ta.w);
+        const bool probe = act && !inval;
+        const bool p1 = probe && lvl == 1, p2 = probe && lvl == 2;
+
+        const Quot q0 = quotient(L0, ta.w, 0, cur);
+        const Quot qa = quotient(L1, ta.w, 0, cur);
+        const Quot qb = quotient(L1, ta.w, 1, cur);
+        const uint64_t e0 = ((ta.compact ? q0.r : cur) << 1) | 1ull;
+        const uint64_t ea = ((ta.compact ? qa.r : cur) << 2) | 1ull;
+        const uint64_t eb = ((ta.compact ? qb.r : cur) << 2) | 2ull;
+        uint64_t *p0 = L0.words + q0.a * kWordsPerBucket + tl * W;
+        uint64_t *pa = L1.words + qa.a * kWordsPerBucket + tl * W;
+        uint64_t *pb = L1.words + qb.a * kWordsPerBucket + tl * W;
+        uint64_t v0[W] = {}, va[W] = {}, vb[W] = {};
+        if (p1) load_relaxed<W>(p0, v0);
+        if (p2) {
+            load_relaxed<W>(pa, va);
+            load_relaxed<W>(pb, vb);
+        }
+        bool m0, ma, mb;
+        int f0, fa, fb;
+        scan_chunk<W, FPW0>(v0, e0, m0, f0);
+        scan_chunk_rt<W>(va, ea, FPW1, ma, fa);
+        scan_chunk_rt<W>(vb, eb, FPW1, mb, fb);
+        const uint32_t bfound = tile_ballot<T>((p1 && m0) || (p2 && (ma || mb)));
+        const uint32_t be0 = tile_ballot<T>(p1 && f0 >= 0);
+        const uint32_t bea = tile_ballot<T>(p2 && fa >= 0);
+        const uint32_t beb = tile_ballot<T>(p2 && fb >= 0);
+        // first empty slot index of each snapshot (B if none)
+        const int la0 = be0 ? __ffs(be0) - 1 : 0;
+        const int laa = bea ? __ffs(bea) - 1 : 0;
+        const int lab = beb ? __ffs(beb) - 1 : 0;
+        const int fe0 = tile_shfl<T>(f0, la0);
+        const int fea = tile_shfl<T>(fa, laa);
+        const int feb = tile_shfl<T>(fb, lab);
+        const int loada = bea ? laa * LF1 + fea : B1;
+        const int loadb = beb ? lab * LF1 + feb : B1;
+        // Definition 1: (1, y) precedes (2, y') iff y < y'; ties go to the second
+        const bool pick_a = loada < loadb;
+        const int load2 = pick_a ? loada : loadb;
+
+        bool want_claim = false;
+        int cl = 0;
+        if (!LOOKUP && !bfound) {
+            if (p1 && be0) {
+                want_claim = true;
+                cl = la0;
+            } else if (p2 && load2 < B1) {
+                want_claim = true;
+                cl = pick_a ? laa : lab;
+            }
+        }
+        bool claimed = false;
+        uint64_t seen = 0;
+        if (!LOOKUP && want_claim && tl == cl) {
+            if (lvl == 1)
+                claimed = claim_field<FPW0>(p0 + f0 / FPW0, f0 % FPW0, pick_word<W>(v0, f0 / FPW0),
+                                            e0, seen, n_fail);
+            else if (pick_a)
+                claimed = claim_field_rt(FPW1, pa + fa / FPW1, fa % FPW1,
+                                         pick_word<W>(va, fa / FPW1), ea, seen, n_fail);
+            else
+                claimed = claim_field_rt(FPW1, pb + fb / FPW1, fb % FPW1,
+                                         pick_word<W>(vb, fb / FPW1), eb, seen, n_fail);
+        }
+        claimed = tile_shfl<T>(claimed, cl);
+        seen = tile_shfl<T>(seen, cl);
+
+        if (act) {
+            bool fin = true;
+            uint8_t st = ST_NOT_FOUND;
+            if (inval) {
+                st = ST_INVALID;
+            } else {
+                n_probe += (lvl == 1) ? 1 : 2;
+                if (bfound) {
+                    st = ST_FOUND;
+                } else if (LOOKUP) {
+                    if (lvl == 1 && !be0) {
+                        fin = false;
+                        lvl = 2;
+                    }
+                } else if (lvl == 1 && !be0) {
+                    fin = false;
+                    lvl = 2;
+                } else if (lvl == 2 && load2 >= B1) {
+                    st = ST_FULL;
+                } else if (claimed) {
+                    st = ST_PUT;
+                    n_write++;
+                } else {
+                    const uint64_t mine = (lvl == 1) ? e0 : (pick_a ? ea : eb);
+                    if (seen == mine) {
+                        st = ST_FOUND;  // another thread inserted k first
+                    } else if (++it > kMaxIter) {
+                        st = ST_ERROR;
+                    } else {
+                        fin = false;  // re-read the bucket(s) at this level
+                    }
+                }
+            }
+            if (fin) {
+                if (tl == 0) {
+                    tw.s_st[tw.q] = st;
+                    if (st == ST_ERROR) atomicOr(ta.err, 1u);
+                    n_ops++;
+                }
+                tw.q++;
+                fresh = true;
+            }
+        }
+        __syncwarp();
+    }
+    if (ta.ctr) {
+        if (tl != 0) n_probe = n_write = 0;
+        flush_counter(ta.ctr, 0, n_probe);
+        flush_counter(ta.ctr, 1, n_write);
+        flush_counter(ta.ctr, 2, (uint64_t)n_fail);
+        flush_counter(ta.ctr, 3, n_ops);
+    }
+}
+
+}  // namespace cht

@@ -1,0 +1,65 @@
+// cht_launch.h - host-side launch helpers shared by the kernel translation
+// units and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "cht_device.cuh"
+
+namespace cht {
+
+struct LaunchParams {
+    int cta;        // threads per block
+    int items;      // keys per thread per chunk
+    int max_ctas;   // 0 = fill the GPU
+    int max_tiles;  // 0 = unbounded
+    int sms;        // multiprocessors of the device
+    cudaStream_t stream;
+};
+
+// resident blocks per SM for a kernel at a given block size and shared memory
+inline int occupancy(const void *kern, int cta, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, size_t>, int> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_tuple(kern, cta, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, cta, smem) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    cache[key] = occ;
+    return occ;
+}
+
+// persistent grid: enough blocks to give every chunk a tile, at most what
+// fits on the GPU at once
+inline int grid_blocks(const void *kern, int T, const LaunchParams &lp, uint64_t n, size_t smem) {
+    const uint64_t per = (uint64_t)T * lp.items;
+    uint64_t chunks = (n + per - 1) / per;
+    if (lp.max_tiles > 0 && chunks > (uint64_t)lp.max_tiles) chunks = lp.max_tiles;
+    const uint64_t tiles_per_block = lp.cta / T;
+    uint64_t need = (chunks + tiles_per_block - 1) / tiles_per_block;
+    uint64_t cap = (uint64_t)lp.sms * occupancy(kern, lp.cta, smem);
+    if (lp.max_ctas > 0 && cap > (uint64_t)lp.max_ctas) cap = lp.max_ctas;
+    uint64_t b = need < cap ? need : cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+cudaError_t launch_cuckoo_insert(int T, int fpw, const LaunchParams &lp, const TableArgs &ta,
+                                 const void *keys, uint64_t n, uint8_t *status,
+                                 uint64_t *dropped);
+cudaError_t launch_cuckoo_find(int T, int fpw, const LaunchParams &lp, const TableArgs &ta,
+                               const void *keys, uint64_t n, uint8_t *status);
+cudaError_t launch_iceberg(int T, int fpw0, bool lookup, const LaunchParams &lp,
+                           const TableArgs &ta, const void *keys, uint64_t n, uint8_t *status);
+
+}  // namespace cht

@@ -1,0 +1,44 @@
+// Instantiations and launcher of the iceberg find-or-put (Algorithm 1) and
+// lookup (Section 2.3) kernels.
+#include "cht_kernels.cuh"
+#include "cht_launch.h"
+
+namespace cht {
+
+template <int T, int FPW0, bool LOOKUP>
+static cudaError_t run(const LaunchParams &lp, const TableArgs &ta, const void *keys, uint64_t n,
+                       uint8_t *status) {
+    auto kern = k_iceberg<T, FPW0, LOOKUP>;
+    const size_t smem = smem_bytes(lp.cta, lp.items);
+    const int blocks = grid_blocks((const void *)kern, T, lp, n, smem);
+    kern<<<blocks, lp.cta, smem, lp.stream>>>(ta, keys, n, status, lp.items);
+    return cudaGetLastError();
+}
+
+template <int T>
+static cudaError_t by_fpw(int fpw0, bool lookup, const LaunchParams &lp, const TableArgs &ta,
+                          const void *keys, uint64_t n, uint8_t *status) {
+    switch (fpw0) {
+        case 1: return lookup ? run<T, 1, true>(lp, ta, keys, n, status)
+                              : run<T, 1, false>(lp, ta, keys, n, status);
+        case 2: return lookup ? run<T, 2, true>(lp, ta, keys, n, status)
+                              : run<T, 2, false>(lp, ta, keys, n, status);
+        case 3: return lookup ? run<T, 3, true>(lp, ta, keys, n, status)
+                              : run<T, 3, false>(lp, ta, keys, n, status);
+        case 4: return lookup ? run<T, 4, true>(lp, ta, keys, n, status)
+                              : run<T, 4, false>(lp, ta, keys, n, status);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_iceberg(int T, int fpw0, bool lookup, const LaunchParams &lp,
+                           const TableArgs &ta, const void *keys, uint64_t n, uint8_t *status) {
+    switch (T) {
+        case 4: return by_fpw<4>(fpw0, lookup, lp, ta, keys, n, status);
+        case 8: return by_fpw<8>(fpw0, lookup, lp, ta, keys, n, status);
+        case 16: return by_fpw<16>(fpw0, lookup, lp, ta, keys, n, status);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cht

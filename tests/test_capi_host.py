@@ -1,0 +1,106 @@
+"""The C-ABI library loads, exports every symbol include/cht.h declares, and
+its host-only planner (configuration resolution, storage size) follows the
+paper's bit budgets. No GPU needed: nothing here launches a kernel."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT, read_golden
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2406_09255_gb300 import build as B
+    B.build()
+    from paper_2406_09255_gb300 import _lib
+    return _lib
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cht.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cht_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    L = lib.load()
+    names = _declared()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(L, name), f"{name} declared in cht.h but not exported"
+    # the binding declares exactly the header's entry points
+    assert sorted(lib.SIGNATURES) == names
+
+
+def test_binding_struct_matches_header_layout(lib):
+    # 4 ints, 2 u64, 4 ints, u64, 5 ints, 3 reserved ints
+    assert ctypes.sizeof(lib.Config) == 4 * 4 + 16 + 4 * 4 + 8 + 5 * 4 + 12
+    assert ctypes.sizeof(lib.Counters) == 32
+
+
+def _resolve(lib, **kw):
+    from paper_2406_09255_gb300.table import _make_config
+    c = _make_config(**kw)
+    out = lib.Config()
+    code = lib.load().cht_resolve_config(ctypes.byref(c), ctypes.byref(out))
+    return code, out
+
+
+def test_workload_layouts(lib):
+    # compact cuckoo, 2^14 buckets, 32-bit keys: 18-bit remainders + 2 tag bits
+    # -> three fields per word, 48 slots per bucket, 786,432 slots
+    code, c = _resolve(lib, kind=0, key_bits=32, key_bytes=4, num_buckets=1 << 14)
+    assert code == 0 and c.fields_per_word == 3 and c.num_hashes == 3
+    assert (1 << 14) * 16 * c.fields_per_word == 786432
+    # 2^24 buckets, 40-bit keys: 16 + 2 bits -> three per word (805,306,368 slots), 2 GiB
+    code, c = _resolve(lib, kind=0, key_bits=40, num_buckets=1 << 24)
+    assert code == 0 and c.fields_per_word == 3
+    assert lib.load().cht_table_bytes(ctypes.byref(c)) == 256 + (1 << 24) * 128
+    # iceberg, 48-bit keys, 2^22 primary (26-bit remainders + flag) and 2^19
+    # secondary buckets (29 bits + 2 tag bits): two 32-bit fields per word
+    code, c = _resolve(lib, kind=1, key_bits=48, num_buckets=1 << 22,
+                       num_buckets_backyard=1 << 19)
+    assert code == 0 and c.fields_per_word == 2 and c.fields_per_word_backyard == 2
+    assert (1 << 22) * 32 + (1 << 19) * 32 == 150994944
+    # whole-key table: 64-bit slots
+    code, c = _resolve(lib, kind=0, key_bits=40, num_buckets=3 << 24, compact=0)
+    assert code == 0 and c.fields_per_word == 1
+
+
+def test_bit_budget_section_5_1(lib):
+    g = {r[0]: int(r[1]) for r in read_golden("bit_budget.txt")}
+    nb0 = 1 << g["primary_buckets_log2"]
+    nb1 = 1 << g["secondary_buckets_log2"]
+    # 16-bit primary slots (4 per word): the widest key that fits is 37 bits
+    code, _ = _resolve(lib, kind=1, key_bits=g["max_key_bits"], num_buckets=nb0,
+                       num_buckets_backyard=nb1, fields_per_word=4, fields_per_word_backyard=2)
+    assert code == 0
+    code, _ = _resolve(lib, kind=1, key_bits=g["max_key_bits"] + 1, num_buckets=nb0,
+                       num_buckets_backyard=nb1, fields_per_word=4, fields_per_word_backyard=2)
+    assert code == lib.CHT_ERR_INVALID
+    # 37-bit keys do not fit 16-bit secondary slots, but fit 32-bit ones
+    code, _ = _resolve(lib, kind=1, key_bits=g["max_key_bits"], num_buckets=nb0,
+                       num_buckets_backyard=nb1, fields_per_word=4, fields_per_word_backyard=4)
+    assert code == lib.CHT_ERR_INVALID
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(kind=2, key_bits=32, num_buckets=16), "kind"),
+    (dict(kind=0, key_bits=40, key_bytes=4, num_buckets=16), "key_bits"),
+    (dict(kind=0, key_bits=32, num_buckets=12), "power of two"),
+    (dict(kind=0, key_bits=32, num_buckets=16, tile=32), "tile"),
+    (dict(kind=0, key_bits=32, num_buckets=16, items_per_thread=9), "items"),
+    (dict(kind=0, key_bits=32, num_buckets=16, cta_threads=48), "cta_threads"),
+    (dict(kind=1, key_bits=32, num_buckets=16, num_buckets_backyard=0), "backyard"),
+    (dict(kind=0, key_bits=62, num_buckets=4, fields_per_word=2), "bits"),
+])
+def test_invalid_configs_rejected_with_message(lib, kw, frag):
+    code, _ = _resolve(lib, **kw)
+    assert code == lib.CHT_ERR_INVALID
+    assert frag in lib.load().cht_last_error().decode()
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.load().cht_version()

@@ -1,0 +1,390 @@
+"""GPU parity: the CUDA path through the C ABI against the sequential oracle.
+
+Contract (what is unique is compared exactly, the rest checked for validity):
+  - A single tile (max_tiles = 1) processes keys strictly in input order, so
+    its table must equal the oracle's word for word, with identical statuses
+    and dropped keys.
+  - Concurrent cuckoo build without FULL: every status PUT, the enumerated
+    set equals the input, lookups equal the oracle's (they depend only on
+    the key set), and the oracle run on the GPU's own table dump reproduces
+    the GPU's lookups and probe counts exactly.
+  - Concurrent cuckoo build with FULL: stored + dropped = input.
+  - Concurrent iceberg find-or-put: exactly one PUT per distinct key, the
+    rest FOUND; the stored set equals the oracle's; the dump is well formed
+    (Theorem 1 (a)); FULL keys have all three buckets full and lack the key.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2406_09255_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0) if torch.cuda.is_available() else None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def cht():
+    import paper_2406_09255_gb300 as m
+    return m
+
+
+def u64(x: torch.Tensor) -> np.ndarray:
+    """Device/host int tensor of keys -> numpy uint64 (4-byte keys zero-extended)."""
+    a = x.detach().cpu().numpy()
+    if a.dtype == np.int32:
+        return a.view(np.uint32).astype(np.uint64)
+    return a.view(np.uint64)
+
+
+def dev_keys(keys64: torch.Tensor, key_bytes: int) -> torch.Tensor:
+    k = W.to_u32(keys64) if key_bytes == 4 else keys64
+    return k.to(DEV)
+
+
+def words(t, level=0) -> np.ndarray:
+    return t.words(level).cpu().numpy().view(np.uint64)
+
+
+def mirror(t):
+    """An oracle table with the resolved geometry of GPU table t."""
+    c = t.cfg
+    return oracle.Table(c.kind, c.key_bits, c.num_buckets, c.num_buckets_backyard,
+                        compact=bool(c.compact), fpw0=c.fields_per_word,
+                        fpw1=max(c.fields_per_word_backyard, 1), num_hashes=max(c.num_hashes, 1),
+                        max_chain=max(c.max_chain, 1), seed=c.seed)
+
+
+def dump_into(o, t):
+    o.load_words(words(t, 0), words(t, 1) if t.cfg.kind == 1 else None)
+    return o
+
+
+# --------------------------------------------------------------------------
+# sequential single-tile runs: bit-exact tables
+# --------------------------------------------------------------------------
+CUCKOO_SEQ = [
+    # (key_bits, key_bytes, log2 buckets, fpw, compact)
+    (24, 8, 6, 3, True),
+    (32, 4, 6, 2, True),
+    (20, 4, 6, 4, True),
+    (40, 8, 6, 1, True),
+    (40, 8, 6, 1, False),
+]
+
+
+@pytest.mark.parametrize("T", [4, 8, 16])
+@pytest.mark.parametrize("geom", CUCKOO_SEQ)
+def test_sequential_cuckoo_bit_exact(T, geom):
+    w, kb, N, fpw, compact = geom
+    C = 24
+    t = cht().Table(cht().CUCKOO, w, 1 << N, key_bytes=kb, fields_per_word=fpw, compact=compact,
+                    max_chain=C, seed=1000 + N, tile=T, items_per_thread=3, max_tiles=1,
+                    cta_threads=32)
+    o = mirror(t)
+    n = t.slots + 64  # more keys than slots: FULL must occur
+    keys = W.unique_keys(0, n, w, 42 + T)
+    # a few invalid keys in the stream
+    keys[5] = 0
+    keys[n // 2] = 1 << w if w < 62 and kb == 8 else 0
+    dropped = torch.zeros(n, dtype=torch.int64, device=DEV)
+    st = t.insert(dev_keys(keys, kb), dropped=dropped)
+    ost, odr = o.insert(keys.numpy().astype(np.uint64))
+    gst = st.cpu().numpy()
+    assert (gst == ost).all()
+    assert (ost == oracle.FULL).sum() > 0, "the case should exercise FULL"
+    full = ost == oracle.FULL
+    assert (dropped.cpu().numpy().view(np.uint64)[full] == odr[full]).all()
+    assert np.array_equal(words(t), o.t0)
+    # lookups on the same table are equal too
+    q = W.unique_keys(0, n + 500, w, 42 + T)
+    assert (t.find(dev_keys(q, kb)).cpu().numpy() == o.find(q.numpy().astype(np.uint64))).all()
+
+
+ICEBERG_SEQ = [
+    # (key_bits, key_bytes, log2 primary, log2 backyard, fpw0, fpw1, compact)
+    (40, 8, 4, 2, 1, 1, True),
+    (32, 4, 4, 2, 2, 2, True),
+    (19, 4, 4, 2, 4, 2, True),
+    (20, 4, 4, 2, 3, 2, True),
+    (40, 8, 4, 2, 1, 1, False),
+]
+
+
+@pytest.mark.parametrize("T", [4, 8, 16])
+@pytest.mark.parametrize("geom", ICEBERG_SEQ)
+def test_sequential_iceberg_bit_exact(T, geom):
+    w, kb, N0, N1, f0, f1, compact = geom
+    t = cht().Table(cht().ICEBERG, w, 1 << N0, 1 << N1, key_bytes=kb, fields_per_word=f0,
+                    fields_per_word_backyard=f1, compact=compact, seed=77 + N0, tile=T,
+                    items_per_thread=2, max_tiles=1, cta_threads=64)
+    o = mirror(t)
+    fresh = W.unique_keys(0, int(1.1 * t.slots), w, 9 + T)
+    rng = np.random.default_rng(T)
+    dup = fresh[torch.from_numpy(rng.integers(0, len(fresh), len(fresh) // 2))]
+    keys = torch.cat([fresh, dup])
+    keys = keys[torch.from_numpy(rng.permutation(len(keys)))]
+    keys[3] = 0
+    st = t.find_or_put(dev_keys(keys, kb)).cpu().numpy()
+    ost = o.insert(keys.numpy().astype(np.uint64))
+    assert (st == ost).all()
+    assert (ost == oracle.FULL).sum() > 0 and (ost == oracle.FOUND).sum() > 0
+    assert np.array_equal(words(t, 0), o.t0)
+    assert np.array_equal(words(t, 1), o.t1)
+    q = W.unique_keys(0, len(fresh) + 300, w, 9 + T)
+    assert (t.find(dev_keys(q, kb)).cpu().numpy() == o.find(q.numpy().astype(np.uint64))).all()
+
+
+# --------------------------------------------------------------------------
+# concurrent cuckoo
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("T,items", [(4, 1), (8, 2), (16, 8), (8, 5)])
+def test_cuckoo_2e14_fill_08_lookup_parity(T, items):
+    """2^14 buckets x 48 slots, 32-bit keys, 629,145 keys (fill 0.8), then 2^20
+    lookups, half present and half absent."""
+    t = cht().Table(cht().CUCKOO, 32, 1 << 14, key_bytes=4, seed=0x2406_0925_5001, tile=T,
+                    items_per_thread=items)
+    assert t.cfg.fields_per_word == 3 and t.slots == 786432
+    n = 629145
+    keys = W.unique_keys(0, n, 32, W.SEED_BASE + 1)
+    st = t.insert(dev_keys(keys, 4)).cpu().numpy()
+    assert (st == cht().PUT).all()
+    assert t.error_flags() == 0
+    stored, cnt = t.enumerate()
+    assert cnt == n
+    assert np.array_equal(np.sort(u64(stored)), np.sort(keys.numpy().astype(np.uint64)))
+
+    q, present = W.find_queries(n, 1 << 20, 0.5, 32, W.SEED_BASE + 1, n)
+    ctr = t.attach_counters()
+    got = t.find(dev_keys(q, 4)).cpu().numpy()
+    gprobes = int(ctr[0].item())
+    t.detach_counters()
+    assert np.array_equal(got == cht().FOUND, present.numpy())
+    # the oracle on its own sequentially built table
+    o = mirror(t)
+    o.insert(keys.numpy().astype(np.uint64))
+    assert (o.find(q.numpy().astype(np.uint64)) == got).all()
+    # the oracle on the GPU's table: same answers and the same probe count
+    d = dump_into(mirror(t), t)
+    assert (d.find(q.numpy().astype(np.uint64)) == got).all()
+    assert d.probes == gprobes
+    assert d.check_prefix() == 0
+    assert d.check_entries() == 0
+    assert d.check_cuckoo_chain() == 0
+
+
+@pytest.mark.parametrize("compact", [True, False])
+def test_cuckoo_past_capacity_conserves_keys(compact):
+    t = cht().Table(cht().CUCKOO, 28, 1 << 10, compact=compact, max_chain=8, seed=3)
+    n = int(0.99 * t.slots)
+    keys = W.unique_keys(0, n, 28, 99)
+    dropped = torch.zeros(n, dtype=torch.int64, device=DEV)
+    st = t.insert(keys.to(DEV), dropped=dropped).cpu().numpy()
+    full = st == cht().FULL
+    assert full.sum() > 0
+    assert ((st == cht().PUT) | full).all()
+    stored, cnt = t.enumerate()
+    lost = dropped.cpu().numpy().view(np.uint64)[full]
+    both = np.sort(np.concatenate([u64(stored), lost]))
+    assert np.array_equal(both, np.sort(keys.numpy().astype(np.uint64)))
+    d = dump_into(mirror(t), t)
+    assert d.check_prefix() == 0 and d.check_entries() == 0 and d.check_cuckoo_chain() == 0
+    # lookups are exact membership
+    stored_set = set(u64(stored).tolist())
+    got = t.find(keys.to(DEV)).cpu().numpy() == cht().FOUND
+    assert np.array_equal(got, np.array([int(k) in stored_set for k in keys.numpy()]))
+
+
+def test_cuckoo_noncompact_equal_slots_fastrange():
+    # whole-key table with a bucket count that is not a power of two
+    nb = 3 * (1 << 8)
+    t = cht().Table(cht().CUCKOO, 40, nb, compact=False, seed=8)
+    assert t.cfg.fields_per_word == 1
+    n = int(0.85 * t.slots)
+    keys = W.unique_keys(0, n, 40, 5)
+    st = t.insert(keys.to(DEV)).cpu().numpy()
+    assert (st == cht().PUT).all()
+    q, present = W.find_queries(n, 20000, 0.5, 40, 5, n)
+    got = t.find(q.to(DEV)).cpu().numpy()
+    assert np.array_equal(got == cht().FOUND, present.numpy())
+    d = dump_into(mirror(t), t)
+    assert (d.find(q.numpy().astype(np.uint64)) == got).all()
+    assert d.check_entries() == 0 and d.check_cuckoo_chain() == 0
+
+
+# --------------------------------------------------------------------------
+# concurrent iceberg find-or-put
+# --------------------------------------------------------------------------
+def _fop_contract(t, keys_np, st, o_stored):
+    """Per-key flags and final set against the oracle's, for a run whose
+    oracle replay had no FULL."""
+    P = cht()
+    assert ((st == P.PUT) | (st == P.FOUND)).all()
+    uniq, inv = np.unique(keys_np, return_inverse=True)
+    puts = np.bincount(inv, weights=(st == P.PUT), minlength=len(uniq))
+    assert (puts == 1).all(), "each distinct key is put exactly once"
+    stored, cnt = t.enumerate()
+    assert np.array_equal(np.sort(u64(stored)), np.sort(o_stored))
+    d = dump_into(mirror(t), t)
+    assert d.check_entries() == 0
+    assert d.check_order_property() == 0
+    assert d.check_prefix() == 0
+    return d
+
+
+@pytest.mark.parametrize("T,items", [(4, 2), (8, 1), (16, 4)])
+def test_iceberg_fop_duplicates_parity(T, items):
+    w = 40
+    t = cht().Table(cht().ICEBERG, w, 1 << 12, 1 << 9, seed=21, tile=T, items_per_thread=items)
+    o = mirror(t)
+    n_fresh = int(0.8 * t.slots)
+    fresh = W.unique_keys(0, n_fresh, w, 55)
+    keys = W.duplicate_stream(2 * n_fresh, n_fresh, w, 55, 0.5)
+    # duplicate_stream draws its fresh keys from the same sequence
+    assert set(keys.numpy().tolist()) == set(fresh.numpy().tolist())
+    st = t.find_or_put(keys.to(DEV)).cpu().numpy()
+    kn = keys.numpy().astype(np.uint64)
+    ost = o.insert(kn)
+    assert (ost != oracle.FULL).all()
+    _fop_contract(t, kn, st, o.enumerate())
+    # lookups after the batch are exact
+    q, present = W.find_queries(n_fresh, 30000, 0.5, w, 55, 2 * n_fresh)
+    got = t.find(q.to(DEV)).cpu().numpy()
+    assert np.array_equal(got == cht().FOUND, present.numpy())
+    assert (o.find(q.numpy().astype(np.uint64)) == got).all()
+    # a second batch of the same keys finds everything
+    st2 = t.find_or_put(keys.to(DEV)).cpu().numpy()
+    assert (st2 == cht().FOUND).all()
+    assert t.error_flags() == 0
+
+
+def test_iceberg_hot_key_contention():
+    # every key repeated 64 times in one batch: CAS races on the same slots
+    t = cht().Table(cht().ICEBERG, 40, 1 << 6, 1 << 3, seed=4)
+    base = W.unique_keys(0, 1000, 40, 7)
+    keys = base.repeat(64)
+    keys = keys[torch.from_numpy(np.random.default_rng(0).permutation(len(keys)))]
+    st = t.find_or_put(keys.to(DEV)).cpu().numpy()
+    o = mirror(t)
+    ost = o.insert(keys.numpy().astype(np.uint64))
+    assert (ost != oracle.FULL).all()
+    _fop_contract(t, keys.numpy().astype(np.uint64), st, o.enumerate())
+
+
+@pytest.mark.parametrize("compact", [True, False])
+def test_iceberg_past_capacity_theorem1(compact):
+    w = 36
+    t = cht().Table(cht().ICEBERG, w, 1 << 8, 1 << 5, compact=compact, seed=17)
+    fresh = W.unique_keys(0, int(1.08 * t.slots), w, 3)
+    rng = np.random.default_rng(1)
+    keys = torch.cat([fresh, fresh[torch.from_numpy(rng.integers(0, len(fresh), len(fresh)))]])
+    keys = keys[torch.from_numpy(rng.permutation(len(keys)))]
+    kn = keys.numpy().astype(np.uint64)
+    st = t.find_or_put(keys.to(DEV)).cpu().numpy()
+    P = cht()
+    assert (st == P.FULL).sum() > 0
+    stored, cnt = t.enumerate()
+    s = u64(stored)
+    assert len(np.unique(s)) == len(s), "no duplicates (Lemma, Appendix A)"
+    d = dump_into(mirror(t), t)
+    assert d.check_entries() == 0 and d.check_order_property() == 0 and d.check_prefix() == 0
+    stored_set = set(s.tolist())
+    # (c) found/put iff present afterwards; (d) one put per stored key
+    present = np.array([int(k) in stored_set for k in kn])
+    assert np.array_equal((st == P.FOUND) | (st == P.PUT), present)
+    uniq, inv = np.unique(kn, return_inverse=True)
+    puts = np.bincount(inv, weights=(st == P.PUT), minlength=len(uniq))
+    assert set(uniq[puts == 1].tolist()) == stored_set and puts.max() == 1
+    # (e) a FULL key's primary and both secondary buckets are full and lack it
+    o = mirror(t)
+    for k in np.unique(kn[st == P.FULL])[:200]:
+        k = int(k)
+        assert k not in stored_set
+        for lvl, j in ((0, 0), (1, 0), (1, 1)):
+            a = o.address(lvl, j, k)
+            assert all(d.slot(lvl, a, y) != 0 for y in range(o.slots_per_bucket(lvl)))
+    # stored + FULL keys = every distinct key
+    full_set = set(kn[st == P.FULL].tolist())
+    assert stored_set | full_set == set(uniq.tolist())
+
+
+# --------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [0, 1, 7, 1001])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_ragged_and_empty_batches(n, kind):
+    t = cht().Table(kind, 30, 1 << 8, 1 << 5 if kind else 0, key_bytes=4, seed=2, tile=8,
+                    items_per_thread=3)
+    keys = W.unique_keys(0, n, 30, 13)
+    st = t.insert(dev_keys(keys, 4)).cpu().numpy()
+    assert len(st) == n and (st == cht().PUT).all()
+    f = t.find(dev_keys(keys, 4)).cpu().numpy()
+    assert (f == cht().FOUND).all()
+    stored, cnt = t.enumerate()
+    assert cnt == n
+
+
+def test_invalid_keys_and_capacity_of_enumerate():
+    t = cht().Table(cht().ICEBERG, 30, 1 << 8, 1 << 5, seed=2)
+    keys = torch.tensor([0, 1 << 30, 5, 6, (1 << 62), 7], dtype=torch.int64, device=DEV)
+    st = t.find_or_put(keys).cpu().numpy().tolist()
+    I, P = cht().INVALID, cht().PUT
+    assert st == [I, I, P, P, I, P]
+    out, cnt = t.enumerate(cap=2)
+    assert cnt == 3 and len(out) == 2
+    assert set(out.cpu().numpy().tolist()) <= {5, 6, 7}
+
+
+def test_find_or_put_unsupported_on_cuckoo():
+    t = cht().Table(cht().CUCKOO, 30, 1 << 8, seed=2)
+    with pytest.raises(cht().ChtError) as e:
+        t.find_or_put(torch.ones(4, dtype=torch.int64, device=DEV))
+    assert e.value.code == 2
+
+
+def test_clear_empties_table():
+    t = cht().Table(cht().CUCKOO, 30, 1 << 8, seed=2)
+    keys = W.unique_keys(0, 1000, 30, 1).to(DEV)
+    t.insert(keys)
+    t.clear()
+    assert t.enumerate()[1] == 0
+    assert (t.find(keys).cpu().numpy() == cht().NOT_FOUND).all()
+
+
+# --------------------------------------------------------------------------
+# full size: 2^24 buckets (2 GiB), the benchmark's launch configuration
+# --------------------------------------------------------------------------
+def test_cuckoo_2e24_full_size_sampled():
+    P = cht()
+    t = P.Table(P.CUCKOO, 40, 1 << 24, seed=2000)
+    assert t.cfg.fields_per_word == 3 and t.slots == 805306368
+    n = int(0.8 * t.slots)  # 644,245,094
+    seed = W.SEED_BASE + 2
+    keys = W.unique_keys(0, n, 40, seed, device=DEV)
+    st = t.insert(keys)
+    assert int((st != P.PUT).sum().item()) == 0
+    del st
+    # enumerate returns exactly the inserted set
+    stored, cnt = t.enumerate()
+    assert cnt == n
+    assert torch.equal(torch.sort(stored)[0], torch.sort(keys)[0])
+    del stored
+    # lookups at 50 % hit: exact membership for all 402,653,184 queries
+    nq = t.slots // 2
+    q, present = W.find_queries(n, nq, 0.5, 40, seed, n, device=DEV)
+    got = t.find(q)
+    assert torch.equal(got == P.FOUND, present)
+    # a sample re-checked by the oracle on the GPU's table
+    d = dump_into(mirror(t), t)
+    idx = torch.randint(0, nq, (200000,), generator=torch.Generator().manual_seed(0))
+    qs = q[idx.to(DEV)].cpu().numpy().view(np.uint64)
+    assert (d.find(qs) == got[idx.to(DEV)].cpu().numpy()).all()
+    assert d.check_prefix() == 0
