@@ -86,13 +86,19 @@ typedef struct cht_table cht_table; /* opaque host handle */
  * max_chain             cuckoo C, eviction steps before a put gives up
  *                       (Algorithm 4); 0 = 128.
  * seed                  all permutation constants derive from it.
- * tile                  threads cooperating on one bucket: 4, 8 or 16 (0 = 8).
+ * tile                  threads cooperating on one bucket: 4, 8 or 16; 0 lets
+ *                       each operation use its fastest width (lookups 8,
+ *                       puts and find-or-puts 4).
  * items_per_thread      keys each thread loads per work chunk, 1..8 (0 = 2).
  * cta_threads           threads per block, a multiple of 32 (0 = 256).
  * max_ctas              upper bound on blocks (0 = enough to fill the GPU).
  * max_tiles             upper bound on tiles that take work (0 = no bound).
  *                       With max_tiles = 1 a single tile processes the keys
  *                       strictly in input order (a sequential run).
+ * lookups_in_flight     lookups a tile keeps in flight at once in
+ *                       cht_find on cuckoo tables: 1, 2 or 4 (0 = 2). More
+ *                       independent bucket loads per tile hide more HBM
+ *                       latency at the cost of registers.
  */
 typedef struct cht_config {
     int32_t kind;
@@ -111,7 +117,8 @@ typedef struct cht_config {
     int32_t cta_threads;
     int32_t max_ctas;
     int32_t max_tiles;
-    int32_t reserved[3];
+    int32_t lookups_in_flight;
+    int32_t reserved[2];
 } cht_config;
 
 /* Device counters a table can accumulate into (see cht_set_counters). */
@@ -153,6 +160,15 @@ int cht_clear(cht_table *t, void *stream);
 
 /* Copy the resolved configuration of a table into *out. Host only. */
 int cht_get_config(const cht_table *t, cht_config *out);
+
+/*
+ * Change how later calls on the table are launched, leaving its contents and
+ * layout alone: only the launch fields of *launch are read (tile,
+ * items_per_thread, cta_threads, max_ctas, max_tiles, lookups_in_flight; zero
+ * selects the default). Used by autotuners. Host only; validates like
+ * cht_resolve_config and leaves the table unchanged on error.
+ */
+int cht_set_launch(cht_table *t, const cht_config *launch);
 
 /*
  * Insert n keys (d_keys, key_bytes each). d_status[i] receives CHT_PUT,

@@ -38,7 +38,8 @@ class Config(ctypes.Structure):
         ("cta_threads", ctypes.c_int32),
         ("max_ctas", ctypes.c_int32),
         ("max_tiles", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("lookups_in_flight", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
     def as_dict(self) -> dict:
@@ -60,6 +61,7 @@ SIGNATURES = {
     "cht_destroy": (ctypes.c_int, [_vp]),
     "cht_clear": (ctypes.c_int, [_vp, _vp]),
     "cht_get_config": (ctypes.c_int, [_vp, _cfgp]),
+    "cht_set_launch": (ctypes.c_int, [_vp, _cfgp]),
     "cht_insert": (ctypes.c_int, [_vp, _vp, _sz, _vp, _vp, _vp]),
     "cht_find": (ctypes.c_int, [_vp, _vp, _sz, _vp, _vp]),
     "cht_find_or_put": (ctypes.c_int, [_vp, _vp, _sz, _vp, _vp]),

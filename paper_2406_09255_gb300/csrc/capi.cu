@@ -120,8 +120,8 @@ int resolve(const cht_config *in, cht_config *out) {
         e = resolve_level(c, 1, c.num_buckets_backyard, c.fields_per_word_backyard);
         if (e) return e;
     }
-    if (c.tile == 0) c.tile = 8;
-    if (c.tile != 4 && c.tile != 8 && c.tile != 16)
+    // tile 0 stays 0: each operation then uses its own best width
+    if (c.tile != 0 && c.tile != 4 && c.tile != 8 && c.tile != 16)
         return fail(CHT_ERR_INVALID, "tile must be 4, 8 or 16 (got %d)", c.tile);
     if (c.items_per_thread == 0) c.items_per_thread = 2;
     if (c.items_per_thread < 1 || c.items_per_thread > 8)
@@ -131,6 +131,9 @@ int resolve(const cht_config *in, cht_config *out) {
         return fail(CHT_ERR_INVALID, "cta_threads must be a multiple of 32 in [32, 256]");
     if (c.max_ctas < 0 || c.max_tiles < 0)
         return fail(CHT_ERR_INVALID, "max_ctas and max_tiles must be >= 0");
+    if (c.lookups_in_flight == 0) c.lookups_in_flight = 2;
+    if (c.lookups_in_flight != 1 && c.lookups_in_flight != 2 && c.lookups_in_flight != 4)
+        return fail(CHT_ERR_INVALID, "lookups_in_flight must be 1, 2 or 4");
     *out = c;
     return CHT_OK;
 }
@@ -155,12 +158,30 @@ void fill_level(Level &L, uint64_t *words, uint64_t nb, int key_bits, int fpw, u
     }
 }
 
+enum Op { kOpCuckooInsert, kOpCuckooFind, kOpIcebergFop, kOpIcebergFind };
+
+// threads per bucket for an operation: the configured tile, or when it is 0
+// the width measured fastest on GB300 for that operation (cuckoo puts keep
+// four lanes per bucket so that more puts are in flight; lookups use eight
+// lanes, one 16-byte read each, so one warp load fetches four whole lines)
+int tile_for(const cht_table *t, Op op) {
+    if (t->cfg.tile) return t->cfg.tile;
+    switch (op) {
+        case kOpCuckooInsert: return 4;
+        case kOpCuckooFind: return 8;
+        case kOpIcebergFop: return 4;
+        case kOpIcebergFind: return 8;
+    }
+    return 8;
+}
+
 LaunchParams launch_params(const cht_table *t, void *stream) {
     LaunchParams lp;
     lp.cta = t->cfg.cta_threads;
     lp.items = t->cfg.items_per_thread;
     lp.max_ctas = t->cfg.max_ctas;
     lp.max_tiles = t->cfg.max_tiles;
+    lp.in_flight = t->cfg.lookups_in_flight;
     lp.sms = t->sms;
     lp.stream = static_cast<cudaStream_t>(stream);
     return lp;
@@ -262,6 +283,23 @@ int cht_get_config(const cht_table *t, cht_config *out) {
     return ok();
 }
 
+int cht_set_launch(cht_table *t, const cht_config *launch) {
+    if (!t || !launch) return fail(CHT_ERR_INVALID, "null argument");
+    cht_config c = t->cfg;
+    c.tile = launch->tile;
+    c.items_per_thread = launch->items_per_thread;
+    c.cta_threads = launch->cta_threads;
+    c.max_ctas = launch->max_ctas;
+    c.max_tiles = launch->max_tiles;
+    c.lookups_in_flight = launch->lookups_in_flight;
+    cht_config r;
+    int e = resolve(&c, &r);
+    if (e) return e;
+    t->cfg = r;
+    t->args.max_tiles = r.max_tiles;
+    return ok();
+}
+
 int cht_insert(cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
                uint64_t *d_dropped, void *stream) {
     int e = check_keys(t, d_keys, n, d_status);
@@ -270,10 +308,10 @@ int cht_insert(cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
     const LaunchParams lp = launch_params(t, stream);
     cudaError_t ce;
     if (t->cfg.kind == CHT_CUCKOO)
-        ce = launch_cuckoo_insert(t->cfg.tile, t->cfg.fields_per_word, lp, t->args, d_keys, n,
+        ce = launch_cuckoo_insert(tile_for(t, kOpCuckooInsert), t->cfg.fields_per_word, lp, t->args, d_keys, n,
                                   d_status, d_dropped);
     else
-        ce = launch_iceberg(t->cfg.tile, t->cfg.fields_per_word, false, lp, t->args, d_keys, n,
+        ce = launch_iceberg(tile_for(t, kOpIcebergFop), t->cfg.fields_per_word, false, lp, t->args, d_keys, n,
                             d_status);
     return ce == cudaSuccess ? ok() : cuda_fail(ce, "insert kernel launch");
 }
@@ -285,10 +323,10 @@ int cht_find(const cht_table *t, const void *d_keys, size_t n, uint8_t *d_status
     const LaunchParams lp = launch_params(t, stream);
     cudaError_t ce;
     if (t->cfg.kind == CHT_CUCKOO)
-        ce = launch_cuckoo_find(t->cfg.tile, t->cfg.fields_per_word, lp, t->args, d_keys, n,
+        ce = launch_cuckoo_find(tile_for(t, kOpCuckooFind), t->cfg.fields_per_word, lp, t->args, d_keys, n,
                                 d_status);
     else
-        ce = launch_iceberg(t->cfg.tile, t->cfg.fields_per_word, true, lp, t->args, d_keys, n,
+        ce = launch_iceberg(tile_for(t, kOpIcebergFind), t->cfg.fields_per_word, true, lp, t->args, d_keys, n,
                             d_status);
     return ce == cudaSuccess ? ok() : cuda_fail(ce, "find kernel launch");
 }
@@ -302,7 +340,7 @@ int cht_find_or_put(cht_table *t, const void *d_keys, size_t n, uint8_t *d_statu
                     "find-or-put is offered by iceberg tables only (cuckoo tables are static)");
     if (n == 0) return ok();
     const LaunchParams lp = launch_params(t, stream);
-    cudaError_t ce = launch_iceberg(t->cfg.tile, t->cfg.fields_per_word, false, lp, t->args,
+    cudaError_t ce = launch_iceberg(tile_for(t, kOpIcebergFop), t->cfg.fields_per_word, false, lp, t->args,
                                     d_keys, n, d_status);
     return ce == cudaSuccess ? ok() : cuda_fail(ce, "find-or-put kernel launch");
 }

@@ -74,7 +74,10 @@ __host__ __device__ __forceinline__ uint64_t splitmix(uint64_t s, uint64_t idx) 
 // multiply-shift hash of r. a = the high n bits of pi_j(k), remainder = r.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t round_fn(const Level &L, int j, uint64_t r) {
-    return L.n ? (L.A[j] * r + L.B[j]) >> (64 - L.n) : 0ull;
+    // select the constants without indexing the parameter block dynamically
+    const uint64_t A = j == 0 ? L.A[0] : (j == 1 ? L.A[1] : L.A[2]);
+    const uint64_t B = j == 0 ? L.B[0] : (j == 1 ? L.B[1] : L.B[2]);
+    return L.n ? (A * r + B) >> (64 - L.n) : 0ull;
 }
 
 __device__ __forceinline__ uint64_t low_mask(int bits) {
@@ -148,6 +151,43 @@ __device__ __forceinline__ void load_readonly(const uint64_t *p, uint64_t (&v)[W
     }
 }
 
+// read-only data that will not be reused soon: non-coherent path, no L1
+// allocation (random bucket lines would only evict each other)
+template <int W>
+__device__ __forceinline__ void load_stream(const uint64_t *p, uint64_t (&v)[W]) {
+    if constexpr (W == 1) {
+        asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v[0]) : "l"(p));
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2)
+            asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];"
+                         : "=l"(v[i]), "=l"(v[i + 1])
+                         : "l"(p + i));
+    }
+}
+
+// load_stream under a predicate: when p is false no load is issued and v keeps
+// its previous contents
+template <int W>
+__device__ __forceinline__ void load_stream_if(bool p, const uint64_t *ptr, uint64_t (&v)[W]) {
+    const unsigned pr = p ? 1u : 0u;
+    if constexpr (W == 1) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+            "@q ld.global.nc.L1::no_allocate.u64 %0, [%1];\n\t}"
+            : "+l"(v[0])
+            : "l"(ptr), "r"(pr));
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2)
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t"
+                "@q ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];\n\t}"
+                : "+l"(v[i]), "+l"(v[i + 1])
+                : "l"(ptr + i), "r"(pr));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Tile primitives. A tile is T consecutive lanes of a warp; every lane of the
 // warp executes these together (full-warp masks), each tile reading its own
@@ -173,42 +213,71 @@ __device__ __forceinline__ bool tile_shfl(bool v, int src) {
     return __shfl_sync(0xffffffffu, (int)v, src, T) != 0;
 }
 
+// Zero-field test on a packed word (the "has a zero byte" bit trick, widened
+// to S-bit fields): (x - LOWS) & ~x & HIGHS has the top bit of field f set
+// when field f is zero and lies below every other zero field; fields above
+// the lowest zero one may be flagged spuriously (a borrow), which neither
+// "any field zero" nor "lowest zero field" can see. No field value in
+// [1, 2^S) is ever flagged without a zero field below it.
+template <int FPW>
+struct Swar {
+    static constexpr int S = 64 / FPW;
+    static constexpr uint64_t LOWS = FPW == 1 ? 1ull
+                                   : FPW == 2 ? 0x0000000100000001ull
+                                   : FPW == 3 ? ((1ull << 42) | (1ull << 21) | 1ull)
+                                              : 0x0001000100010001ull;
+    static constexpr uint64_t HIGHS = LOWS << (S - 1);
+    __device__ __forceinline__ static uint64_t zeros(uint64_t x) {
+        return (x - LOWS) & ~x & HIGHS;
+    }
+    // entry replicated into every field of a word
+    __device__ __forceinline__ static uint64_t spread(uint64_t entry) { return entry * LOWS; }
+};
+
 // per-lane scan of the owned fields: whether one equals `entry`, and the local
 // index of the first EMPTY field (-1 if none)
 template <int W, int FPW>
 __device__ __forceinline__ void scan_chunk(const uint64_t (&v)[W], uint64_t entry, bool &match,
                                            int &first_empty) {
-    match = false;
+    using Z = Swar<FPW>;
+    const uint64_t pat = Z::spread(entry);
+    uint64_t hit = 0;
     first_empty = -1;
 #pragma unroll
     for (int i = W - 1; i >= 0; --i) {
-#pragma unroll
-        for (int f = FPW - 1; f >= 0; --f) {
-            uint64_t x = Fields<FPW>::get(v[i], f);
-            match |= (x == entry);
-            if (x == 0) first_empty = i * FPW + f;
-        }
+        hit |= Z::zeros(v[i] ^ pat);
+        const uint64_t z = Z::zeros(v[i]);
+        if (z) first_empty = i * FPW + (__ffsll((long long)z) - 1) / Z::S;
     }
+    match = hit != 0;
+}
+
+// lookup form of the scan: whether some owned field equals `entry`, and
+// whether the lane's last field is EMPTY. Filled slots of a bucket always
+// form a prefix (a claim only succeeds on the first empty slot and no field
+// is ever emptied), so the bucket has room exactly when its last slot,
+// owned by the tile's last lane, is empty.
+template <int W, int FPW>
+__device__ __forceinline__ void probe_chunk(const uint64_t (&v)[W], uint64_t entry, bool &match,
+                                            bool &last_empty) {
+    using Z = Swar<FPW>;
+    const uint64_t pat = Z::spread(entry);
+    uint64_t hm = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) hm |= Z::zeros(v[i] ^ pat);
+    match = hm != 0;
+    last_empty = Fields<FPW>::get(v[W - 1], FPW - 1) == 0;
 }
 
 // the same with the packing known only at run time (fpw in 1..4)
 template <int W>
 __device__ __forceinline__ void scan_chunk_rt(const uint64_t (&v)[W], uint64_t entry, int fpw,
                                               bool &match, int &first_empty) {
-    const int S = 64 / fpw;
-    const uint64_t M = (S >= 64) ? ~0ull : ((1ull << S) - 1ull);
-    match = false;
-    first_empty = -1;
-#pragma unroll
-    for (int i = W - 1; i >= 0; --i) {
-#pragma unroll
-        for (int f = 3; f >= 0; --f) {
-            if (f < fpw) {
-                uint64_t x = (v[i] >> (f * S)) & M;
-                match |= (x == entry);
-                if (x == 0) first_empty = i * fpw + f;
-            }
-        }
+    switch (fpw) {
+        case 1: scan_chunk<W, 1>(v, entry, match, first_empty); break;
+        case 2: scan_chunk<W, 2>(v, entry, match, first_empty); break;
+        case 3: scan_chunk<W, 3>(v, entry, match, first_empty); break;
+        default: scan_chunk<W, 4>(v, entry, match, first_empty); break;
     }
 }
 
@@ -351,7 +420,7 @@ struct TileWork {
         const int tib = threadIdx.x / T;
         items = items_;
         s_keys = smem_keys + (size_t)tib * T * items;
-        s_st = smem_st + (size_t)tib * T * items;
+        s_st = smem_st ? smem_st + (size_t)tib * T * items : nullptr;
         const uint64_t tile_id = (uint64_t)blockIdx.x * tiles_per_block + tib;
         uint64_t ntiles = (uint64_t)gridDim.x * tiles_per_block;
         if (max_tiles > 0 && ntiles > (uint64_t)max_tiles) ntiles = max_tiles;
@@ -376,6 +445,28 @@ struct TileWork {
             }
             chunk += stride;
         }
+        if (chunk >= nchunks) {
+            done = true;
+            qn = q = 0;
+            return;
+        }
+        base = chunk * per;
+        uint64_t rem = n - base;
+        qn = rem < per ? (int)rem : (int)per;
+        q = 0;
+        for (int i = 0; i < items; ++i) {
+            int idx = i * T + tl;
+            if (idx < qn) s_keys[idx] = load_key(keys, key_bytes, base + idx);
+        }
+    }
+
+    // stage the next chunk's keys for kernels that write statuses directly
+    // (no staged statuses to flush); called with q >= qn by every lane of
+    // the tile
+    __device__ __forceinline__ void stage(const void *keys, int key_bytes, uint64_t n) {
+        const int tl = threadIdx.x & (T - 1);
+        const uint64_t per = (uint64_t)T * items;
+        if (qn > 0) chunk += stride;
         if (chunk >= nchunks) {
             done = true;
             qn = q = 0;

@@ -7,6 +7,8 @@
 // carried in predicates, so every ballot and shuffle is a full-warp one.
 #pragma once
 
+#include <type_traits>
+
 #include "cht_device.cuh"
 
 namespace cht {
@@ -149,72 +151,103 @@ __global__ void __launch_bounds__(256)
 // ===========================================================================
 // Compact cuckoo lookup, Section 4.4: probe a_0, a_1, ... for (r_j, j); stop
 // at the first bucket that holds it (FOUND) or that is not full (NOT_FOUND).
-// The table is not written while a lookup runs (static table), so buckets
-// are read through the read-only path.
+//
+// Work sharing as in Algorithm 3, with the per-key arithmetic taken out of
+// the tile: every lane loads one key of the warp's 32 and computes its own
+// bucket address and entry; then each tile of T lanes walks the keys of its
+// own lanes, U at a time. It broadcasts their addresses (Shuffle), loads the
+// U buckets back to back (for T = 8 one 16-byte read per lane and bucket, so
+// one warp load instruction fetches four whole lines) and answers each key
+// with two ballots (Any match, Any empty). A key whose bucket was full and
+// did not hold it moves to hash j + 1 in the next pass. The table is not
+// written while a lookup runs (static table), so buckets are read through
+// the non-coherent path without L1 allocation.
 // ===========================================================================
-template <int T, int FPW>
-__global__ void __launch_bounds__(256)
+template <int T, int FPW, int U>
+__global__ void __launch_bounds__(256, U == 1 ? 6 : (U == 2 ? 5 : 4))
     k_cuckoo_find(TableArgs ta, const void *__restrict__ keys, uint64_t n,
-                  uint8_t *__restrict__ status, int items) {
+                  uint8_t *__restrict__ status) {
     constexpr int W = kWordsPerBucket / T;
-    extern __shared__ uint64_t smem[];
-    TileWork<T> tw;
-    tw.init(smem, reinterpret_cast<uint8_t *>(smem + (size_t)blockDim.x * items), items, n,
-            ta.max_tiles);
-    const int tl = threadIdx.x & (T - 1);
+    // compact entries fit 32 bits when fields are at most 32 bits wide
+    using Entry = typename std::conditional<(FPW >= 2), uint32_t, uint64_t>::type;
+    const int lane = threadIdx.x & 31;
+    const int tl = lane & (T - 1);
+    const int tbase = lane & ~(T - 1);
+    const uint32_t tmask = (T == 32 ? 0xffffffffu : ((1u << T) - 1u)) << tbase;
+    const uint32_t last_lane = 1u << (tbase + T - 1);
     const Level &L = ta.lv[0];
-    uint64_t cur = 0;
-    int j = 0;
-    bool fresh = true;
+    const uint64_t *words = L.words + tl * W;  // this lane's part of every bucket
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) << 5;
     uint64_t n_probe = 0, n_ops = 0;
+    uint64_t v[U][W];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[u][i] = 0;
 
-    while (__any_sync(0xffffffffu, !tw.done)) {
-        if (!tw.done && tw.q >= tw.qn) tw.refill(keys, ta.key_bytes, n, status);
-        __syncwarp();
-        const bool act = !tw.done;
-        if (act && fresh) {
-            cur = tw.s_keys[tw.q];
-            j = 0;
-            fresh = false;
-        }
-        const bool inval = act && !valid_key(cur, ta.w);
-        const bool probe = act && !inval;
-        const Quot qt = quotient(L, ta.w, j, cur);
-        const uint64_t entry = ((ta.compact ? qt.r : cur) << 2) | (uint64_t)(j + 1);
-        uint64_t v[W] = {};
-        if (probe) load_readonly<W>(L.words + qt.a * kWordsPerBucket + tl * W, v);
-        bool m;
-        int fe;
-        scan_chunk<W, FPW>(v, entry, m, fe);
-        const uint32_t bm = tile_ballot<T>(probe && m);
-        const uint32_t be = tile_ballot<T>(probe && fe >= 0);
-        if (act) {
-            bool fin = true;
-            uint8_t st = ST_NOT_FOUND;
-            if (inval) {
-                st = ST_INVALID;
-            } else {
-                n_probe++;
-                if (bm)
-                    st = ST_FOUND;
-                else if (!be && j + 1 < ta.H) {
-                    fin = false;
-                    j++;
+    uint64_t base = warp * 32;
+    uint64_t k_next = (base + lane < n) ? load_key(keys, ta.key_bytes, base + lane) : 0;
+    for (; base < n; base += stride) {
+        const uint64_t idx = base + lane;
+        const bool has = idx < n;
+        const uint64_t k = k_next;
+        // fetch the next chunk's key now; it arrives while this chunk runs
+        const uint64_t nidx = idx + stride;
+        k_next = (nidx < n) ? load_key(keys, ta.key_bytes, nidx) : 0;
+        bool pending = has && valid_key(k, ta.w);
+        uint8_t st = pending ? ST_NOT_FOUND : ST_INVALID;
+        int j = 0;
+        while (__any_sync(0xffffffffu, pending)) {
+            uint32_t addr = 0;  // bucket index (a table has fewer than 2^32 buckets)
+            Entry entry = 0;
+            if (pending) {
+                const Quot qt = quotient(L, ta.w, j, k);
+                addr = (uint32_t)qt.a;
+                entry = (Entry)((((ta.compact ? qt.r : k)) << 2) | (uint64_t)(j + 1));
+            }
+            // this pass: every key of the tile still pending, at its own hash j
+            uint32_t pm = tile_ballot<T>(pending);
+            while (__any_sync(0xffffffffu, pm != 0)) {
+                int r[U];
+                Entry e[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    r[u] = pm ? __ffs(pm) - 1 : -1;
+                    pm &= pm - 1;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int src = r[u] & (T - 1);
+                    const uint32_t a = tile_shfl<T>(addr, src);
+                    e[u] = tile_shfl<T>(entry, src);
+                    load_stream_if<W>(r[u] >= 0, words + (uint64_t)a * kWordsPerBucket, v[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    bool m, le;
+                    probe_chunk<W, FPW>(v[u], e[u], m, le);
+                    const bool live = r[u] >= 0;
+                    const uint32_t bm = __ballot_sync(0xffffffffu, live && m) & tmask;
+                    const uint32_t be = __ballot_sync(0xffffffffu, live && le) & last_lane;
+                    if (tl == r[u]) {
+                        n_probe++;
+                        if (bm) {
+                            st = ST_FOUND;
+                            pending = false;
+                        } else if (be || j + 1 >= ta.H) {
+                            pending = false;
+                        } else {
+                            j++;
+                        }
+                    }
                 }
             }
-            if (fin) {
-                if (tl == 0) {
-                    tw.s_st[tw.q] = st;
-                    n_ops++;
-                }
-                tw.q++;
-                fresh = true;
-            }
         }
-        __syncwarp();
+        if (has) status[idx] = st;
+        n_ops += has ? 1 : 0;
     }
     if (ta.ctr) {
-        if (tl != 0) n_probe = 0;
         flush_counter(ta.ctr, 0, n_probe);
         flush_counter(ta.ctr, 3, n_ops);
     }

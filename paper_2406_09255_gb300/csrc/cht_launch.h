@@ -18,6 +18,7 @@ struct LaunchParams {
     int items;      // keys per thread per chunk
     int max_ctas;   // 0 = fill the GPU
     int max_tiles;  // 0 = unbounded
+    int in_flight;  // lookups a tile keeps in flight (cuckoo lookup)
     int sms;        // multiprocessors of the device
     cudaStream_t stream;
 };
@@ -49,6 +50,17 @@ inline int grid_blocks(const void *kern, int T, const LaunchParams &lp, uint64_t
     const uint64_t tiles_per_block = lp.cta / T;
     uint64_t need = (chunks + tiles_per_block - 1) / tiles_per_block;
     uint64_t cap = (uint64_t)lp.sms * occupancy(kern, lp.cta, smem);
+    if (lp.max_ctas > 0 && cap > (uint64_t)lp.max_ctas) cap = lp.max_ctas;
+    uint64_t b = need < cap ? need : cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+// persistent grid for kernels that give each warp 32 keys at a time
+inline int grid_blocks_warp(const void *kern, const LaunchParams &lp, uint64_t n) {
+    const uint64_t warps = (n + 31) / 32;
+    const uint64_t per_block = lp.cta / 32;
+    uint64_t need = (warps + per_block - 1) / per_block;
+    uint64_t cap = (uint64_t)lp.sms * occupancy(kern, lp.cta, 0);
     if (lp.max_ctas > 0 && cap > (uint64_t)lp.max_ctas) cap = lp.max_ctas;
     uint64_t b = need < cap ? need : cap;
     return b < 1 ? 1 : (int)b;

@@ -18,7 +18,7 @@ __all__ = ["Table", "CUCKOO", "ICEBERG", "resolve_config", "table_bytes"]
 def _make_config(kind, key_bits, num_buckets, num_buckets_backyard=0, *, compact=True,
                  key_bytes=8, fields_per_word=0, fields_per_word_backyard=0, num_hashes=0,
                  max_chain=0, seed=0, tile=0, items_per_thread=0, cta_threads=0, max_ctas=0,
-                 max_tiles=0) -> Config:
+                 max_tiles=0, lookups_in_flight=0) -> Config:
     c = Config()
     c.kind, c.compact, c.key_bits, c.key_bytes = kind, int(compact), key_bits, key_bytes
     c.num_buckets, c.num_buckets_backyard = num_buckets, num_buckets_backyard
@@ -27,6 +27,7 @@ def _make_config(kind, key_bits, num_buckets, num_buckets_backyard=0, *, compact
     c.seed = seed & 0xFFFFFFFFFFFFFFFF
     c.tile, c.items_per_thread, c.cta_threads = tile, items_per_thread, cta_threads
     c.max_ctas, c.max_tiles = max_ctas, max_tiles
+    c.lookups_in_flight = lookups_in_flight
     return c
 
 
@@ -104,6 +105,15 @@ class Table:
 
     def clear(self, stream=None):
         check(self._L.cht_clear(self._h, _stream_handle(stream)))
+
+    def set_launch(self, tile=0, items_per_thread=0, cta_threads=0, max_ctas=0, max_tiles=0,
+                   lookups_in_flight=0):
+        """Change the launch shape of later calls (contents stay)."""
+        c = Config()
+        c.tile, c.items_per_thread, c.cta_threads = tile, items_per_thread, cta_threads
+        c.max_ctas, c.max_tiles, c.lookups_in_flight = max_ctas, max_tiles, lookups_in_flight
+        check(self._L.cht_set_launch(self._h, ctypes.byref(c)))
+        check(self._L.cht_get_config(self._h, ctypes.byref(self.cfg)))
 
     # -- operations -----------------------------------------------------------
     def _prep(self, keys: torch.Tensor, out):

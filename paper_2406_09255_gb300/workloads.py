@@ -174,25 +174,29 @@ def permutation(n: int, seed: int, device="cpu", start: int = 0,
 
 def find_queries(n_inserted: int, n_queries: int, hit_rate: float,
                  key_bits: int, seed: int, absent_base: int,
-                 device="cpu") -> tuple[torch.Tensor, torch.Tensor]:
+                 device="cpu", shuffle_seed: int | None = None
+                 ) -> tuple[torch.Tensor, torch.Tensor]:
     """A shuffled mix of present and absent lookup keys.
 
-    floor(hit_rate * n_queries) queries are distinct inserted keys (key indices
-    below n_inserted, chosen by a seeded permutation); the rest are distinct
-    keys with indices from absent_base upward, which were never inserted.
-    Returns (keys int64, expected_present bool)."""
+    Keys come from the key sequence of `seed` (the one the table was filled
+    from). floor(hit_rate * n_queries) queries are distinct inserted keys (key
+    indices below n_inserted, chosen by a seeded permutation); the rest are
+    distinct keys with indices from absent_base upward, which were never
+    inserted. shuffle_seed (default: seed) only varies which keys are picked
+    and their order. Returns (keys int64, expected_present bool)."""
     n_hit = int(math.floor(hit_rate * n_queries + 1e-9))
     assert n_hit <= n_inserted
     assert absent_base >= n_inserted
+    ss = seed if shuffle_seed is None else shuffle_seed
     idx = torch.empty(n_queries, dtype=torch.int64, device=device)
     if n_hit:
-        idx[:n_hit] = permutation(n_inserted, seed + 1, device, 0, n_hit)
+        idx[:n_hit] = permutation(n_inserted, ss + 1, device, 0, n_hit)
     if n_queries - n_hit:
         idx[n_hit:] = torch.arange(absent_base, absent_base + n_queries - n_hit,
                                    dtype=torch.int64, device=device)
     present = torch.zeros(n_queries, dtype=torch.bool, device=device)
     present[:n_hit] = True
-    pos = permutation(n_queries, seed + 2, device)
+    pos = permutation(n_queries, ss + 2, device)
     q = torch.empty_like(idx)
     q[pos] = idx
     pr = torch.empty_like(present)

@@ -35,8 +35,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_binding_struct_matches_header_layout(lib):
-    # 4 ints, 2 u64, 4 ints, u64, 5 ints, 3 reserved ints
-    assert ctypes.sizeof(lib.Config) == 4 * 4 + 16 + 4 * 4 + 8 + 5 * 4 + 12
+    # 4 ints, 2 u64, 4 ints, u64, 6 ints, 2 reserved ints
+    assert ctypes.sizeof(lib.Config) == 4 * 4 + 16 + 4 * 4 + 8 + 6 * 4 + 8
     assert ctypes.sizeof(lib.Counters) == 32
 
 

@@ -145,12 +145,12 @@ def test_sequential_iceberg_bit_exact(T, geom):
 # --------------------------------------------------------------------------
 # concurrent cuckoo
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("T,items", [(4, 1), (8, 2), (16, 8), (8, 5)])
-def test_cuckoo_2e14_fill_08_lookup_parity(T, items):
+@pytest.mark.parametrize("T,items,P", [(4, 1, 1), (8, 2, 2), (16, 8, 4), (8, 5, 4), (4, 3, 2)])
+def test_cuckoo_2e14_fill_08_lookup_parity(T, items, P):
     """2^14 buckets x 48 slots, 32-bit keys, 629,145 keys (fill 0.8), then 2^20
     lookups, half present and half absent."""
     t = cht().Table(cht().CUCKOO, 32, 1 << 14, key_bytes=4, seed=0x2406_0925_5001, tile=T,
-                    items_per_thread=items)
+                    items_per_thread=items, lookups_in_flight=P)
     assert t.cfg.fields_per_word == 3 and t.slots == 786432
     n = 629145
     keys = W.unique_keys(0, n, 32, W.SEED_BASE + 1)
