@@ -229,6 +229,63 @@ int cht_set_counters(cht_table *t, cht_counters *d_counters);
  */
 int cht_error_flags(const cht_table *t, uint32_t *flags, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Fused multi-table batches                                                 */
+/* ------------------------------------------------------------------------ */
+/*
+ * A batch applies one operation to many iceberg tables, each with its own key
+ * array, in ONE persistent kernel launch: the chunks of all tables form one
+ * index space that every tile walks, so small and large batches share the GPU
+ * instead of each paying a launch and a tail. The operation is Algorithm 1
+ * (find-or-put) or the Section 2.3 lookup, per key exactly as cht_find_or_put
+ * and cht_find on that table.
+ *
+ * All tables of a batch must be iceberg tables on the current device with the
+ * same primary packing (fields_per_word). Tables, key arrays and status arrays
+ * must stay alive, and no table may appear twice, for as long as the batch is
+ * launched. A table may be written by only one batch or call at a time.
+ */
+typedef struct cht_batch cht_batch; /* opaque host handle */
+
+#define CHT_OP_FIND_OR_PUT 0
+#define CHT_OP_FIND 1
+
+/* Device scratch bytes a batch of count tables needs (its descriptors). */
+size_t cht_batch_scratch_bytes(int count);
+
+/*
+ * Plan a batch: count (1..16384) entries of (tables[i], d_keys[i], n[i],
+ * d_status[i]). The descriptors are written into the caller-owned device
+ * scratch d_scratch (at least cht_batch_scratch_bytes(count) bytes, 16-byte
+ * aligned) by a copy enqueued on stream; the scratch must stay untouched until
+ * cht_batch_destroy. Launch shape: tile 4, 2 items per thread, 256 threads
+ * per block unless changed with cht_batch_set_launch.
+ */
+int cht_batch_create(cht_table *const *tables, const void *const *d_keys, const size_t *n,
+                     uint8_t *const *d_status, int count, int op, void *d_scratch,
+                     size_t scratch_bytes, void *stream, cht_batch **out);
+
+/* Change the launch shape (tile, items_per_thread, cta_threads, max_ctas of
+ * *launch; zero = default). Drops a captured graph. Host only. */
+int cht_batch_set_launch(cht_batch *b, const cht_config *launch);
+
+/* Enqueue the fused launch on stream (capturable in a CUDA graph). */
+int cht_batch_launch(const cht_batch *b, void *stream);
+
+/*
+ * Capture one fused launch into a CUDA graph owned by the batch (on an
+ * internal stream; stream only orders the capture after earlier work) and
+ * instantiate it. cht_batch_replay then launches the graph on any stream.
+ */
+int cht_batch_capture(cht_batch *b, void *stream);
+int cht_batch_replay(const cht_batch *b, void *stream);
+
+/* Empty every table of the batch (zero buckets and headers) in one launch. */
+int cht_batch_clear(const cht_batch *b, void *stream);
+
+/* Free the batch handle and its graph (the scratch stays the caller's). */
+int cht_batch_destroy(cht_batch *b);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *cht_last_error(void);
 

@@ -68,6 +68,17 @@ SIGNATURES = {
     "cht_enumerate": (ctypes.c_int, [_vp, _vp, _sz, _vp, _vp]),
     "cht_set_counters": (ctypes.c_int, [_vp, _vp]),
     "cht_error_flags": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32), _vp]),
+    "cht_batch_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "cht_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_vp),
+                                        ctypes.c_int, ctypes.c_int, _vp, _sz, _vp,
+                                        ctypes.POINTER(_vp)]),
+    "cht_batch_set_launch": (ctypes.c_int, [_vp, _cfgp]),
+    "cht_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "cht_batch_capture": (ctypes.c_int, [_vp, _vp]),
+    "cht_batch_replay": (ctypes.c_int, [_vp, _vp]),
+    "cht_batch_clear": (ctypes.c_int, [_vp, _vp]),
+    "cht_batch_destroy": (ctypes.c_int, [_vp]),
     "cht_last_error": (ctypes.c_char_p, []),
     "cht_version": (ctypes.c_char_p, []),
 }

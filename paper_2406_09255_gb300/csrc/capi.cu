@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "cht.h"
 #include "cht_kernels.cuh"
@@ -385,5 +386,209 @@ int cht_error_flags(const cht_table *t, uint32_t *flags, void *stream) {
 const char *cht_last_error(void) { return g_err.c_str(); }
 
 const char *cht_version(void) { return "cht 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Fused multi-table batches
+// ---------------------------------------------------------------------------
+struct cht_batch {
+    std::vector<BatchDesc> host;   // descriptors as uploaded
+    BatchDesc *dev;                // caller's scratch
+    int count;
+    int op;
+    int fpw0;
+    int device;
+    int sms;
+    cht_config launch;             // tile, items_per_thread, cta_threads, max_ctas
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+int batch_launch_params(const cht_batch *b, void *stream, LaunchParams &lp, int &T,
+                        uint64_t &chunks) {
+    lp.cta = b->launch.cta_threads ? b->launch.cta_threads : 256;
+    lp.items = b->launch.items_per_thread ? b->launch.items_per_thread : 2;
+    lp.max_ctas = b->launch.max_ctas;
+    lp.max_tiles = 0;
+    lp.in_flight = 1;
+    lp.sms = b->sms;
+    lp.stream = static_cast<cudaStream_t>(stream);
+    T = b->launch.tile ? b->launch.tile : 4;
+    const uint64_t per = (uint64_t)T * lp.items;
+    chunks = 0;
+    for (const BatchDesc &d : b->host) chunks += (d.n + per - 1) / per;
+    return CHT_OK;
+}
+
+void drop_graph(cht_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+int check_batch_launch(const cht_config &l) {
+    if (l.tile != 0 && l.tile != 4 && l.tile != 8 && l.tile != 16)
+        return fail(CHT_ERR_INVALID, "tile must be 4, 8 or 16 (got %d)", l.tile);
+    if (l.items_per_thread < 0 || l.items_per_thread > 8)
+        return fail(CHT_ERR_INVALID, "items_per_thread must be 1..8");
+    if (l.cta_threads != 0 && (l.cta_threads < 32 || l.cta_threads > 256 || l.cta_threads % 32))
+        return fail(CHT_ERR_INVALID, "cta_threads must be a multiple of 32 in [32, 256]");
+    if (l.max_ctas < 0) return fail(CHT_ERR_INVALID, "max_ctas must be >= 0");
+    return CHT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t cht_batch_scratch_bytes(int count) {
+    if (count < 1 || count > 16384) return 0;
+    return (size_t)count * sizeof(BatchDesc);
+}
+
+int cht_batch_create(cht_table *const *tables, const void *const *d_keys, const size_t *n,
+                     uint8_t *const *d_status, int count, int op, void *d_scratch,
+                     size_t scratch_bytes, void *stream, cht_batch **out) {
+    if (!out) return fail(CHT_ERR_INVALID, "null output handle pointer");
+    *out = nullptr;
+    if (!tables || !d_keys || !n || !d_status)
+        return fail(CHT_ERR_INVALID, "null batch array");
+    if (count < 1 || count > 16384) return fail(CHT_ERR_INVALID, "count must be 1..16384");
+    if (op != CHT_OP_FIND_OR_PUT && op != CHT_OP_FIND)
+        return fail(CHT_ERR_INVALID, "op must be CHT_OP_FIND_OR_PUT or CHT_OP_FIND");
+    if (!d_scratch || (uintptr_t)d_scratch % 16)
+        return fail(CHT_ERR_INVALID, "scratch must be a 16-byte aligned device pointer");
+    if (scratch_bytes < cht_batch_scratch_bytes(count))
+        return fail(CHT_ERR_CAPACITY, "scratch of %zu bytes is below the %zu needed",
+                    scratch_bytes, cht_batch_scratch_bytes(count));
+    cht_batch *b = new cht_batch();
+    b->count = count;
+    b->op = op;
+    b->dev = static_cast<BatchDesc *>(d_scratch);
+    b->graph = nullptr;
+    b->exec = nullptr;
+    memset(&b->launch, 0, sizeof b->launch);
+    b->host.resize(count);
+    for (int i = 0; i < count; ++i) {
+        const cht_table *t = tables[i];
+        if (!t) {
+            delete b;
+            return fail(CHT_ERR_INVALID, "null table at batch entry %d", i);
+        }
+        if (t->cfg.kind != CHT_ICEBERG) {
+            delete b;
+            return fail(CHT_ERR_UNSUPPORTED, "batch entry %d is not an iceberg table", i);
+        }
+        if (i == 0) {
+            b->fpw0 = t->cfg.fields_per_word;
+            b->device = t->device;
+            b->sms = t->sms;
+        } else if (t->cfg.fields_per_word != b->fpw0 || t->device != b->device) {
+            delete b;
+            return fail(CHT_ERR_UNSUPPORTED,
+                        "batch entry %d differs in primary packing or device from entry 0", i);
+        }
+        if (n[i] && (!d_keys[i] || !d_status[i])) {
+            delete b;
+            return fail(CHT_ERR_INVALID, "null keys or statuses at batch entry %d", i);
+        }
+        if ((uintptr_t)d_keys[i] % t->cfg.key_bytes) {
+            delete b;
+            return fail(CHT_ERR_INVALID, "keys of batch entry %d not aligned", i);
+        }
+        b->host[i].ta = t->args;
+        b->host[i].ta.max_tiles = 0;
+        b->host[i].ta.ctr = nullptr;
+        b->host[i].keys = d_keys[i];
+        b->host[i].n = n[i];
+        b->host[i].status = d_status[i];
+    }
+    cudaError_t ce = cudaMemcpyAsync(b->dev, b->host.data(), sizeof(BatchDesc) * count,
+                                     cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+    if (ce != cudaSuccess) {
+        delete b;
+        return cuda_fail(ce, "uploading batch descriptors");
+    }
+    *out = b;
+    return ok();
+}
+
+int cht_batch_set_launch(cht_batch *b, const cht_config *launch) {
+    if (!b || !launch) return fail(CHT_ERR_INVALID, "null argument");
+    int e = check_batch_launch(*launch);
+    if (e) return e;
+    b->launch = *launch;
+    drop_graph(b);
+    return ok();
+}
+
+int cht_batch_launch(const cht_batch *b, void *stream) {
+    if (!b) return fail(CHT_ERR_INVALID, "null batch");
+    LaunchParams lp;
+    int T;
+    uint64_t chunks;
+    batch_launch_params(b, stream, lp, T, chunks);
+    if (chunks == 0) return ok();
+    cudaError_t ce = launch_iceberg_batch(T, b->fpw0, b->op == CHT_OP_FIND, lp, b->dev, b->count,
+                                          chunks, nullptr);
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "batch kernel launch");
+}
+
+int cht_batch_capture(cht_batch *b, void *stream) {
+    if (!b) return fail(CHT_ERR_INVALID, "null batch");
+    drop_graph(b);
+    cudaStream_t cs;
+    cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return cuda_fail(ce, "creating the capture stream");
+    // order the capture after the caller's earlier work (descriptor upload)
+    ce = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (ce == cudaSuccess) ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_fail(ce, "beginning the capture");
+    }
+    int e = cht_batch_launch(b, cs);
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (e) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "ending the capture");
+    cudaGraphExec_t x = nullptr;
+    ce = cudaGraphInstantiate(&x, g, 0);
+    if (ce != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ce, "instantiating the graph");
+    }
+    b->graph = g;
+    b->exec = x;
+    return ok();
+}
+
+int cht_batch_replay(const cht_batch *b, void *stream) {
+    if (!b) return fail(CHT_ERR_INVALID, "null batch");
+    if (!b->exec) return fail(CHT_ERR_INVALID, "batch has no captured graph");
+    cudaError_t ce = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "graph launch");
+}
+
+int cht_batch_clear(const cht_batch *b, void *stream) {
+    if (!b) return fail(CHT_ERR_INVALID, "null batch");
+    k_clear_batch<<<b->sms * 4, 256, 0, static_cast<cudaStream_t>(stream)>>>(b->dev, b->count);
+    cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "batch clear launch");
+}
+
+int cht_batch_destroy(cht_batch *b) {
+    if (b) drop_graph(b);
+    delete b;
+    return ok();
+}
 
 }  // extern "C"

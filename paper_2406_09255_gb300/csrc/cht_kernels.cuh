@@ -264,27 +264,109 @@ __global__ void __launch_bounds__(256, U == 1 ? 6 : (U == 2 ? 5 : 4))
 // empty slot. A failed CAS re-inspects the winning value and, unless it is
 // k's own entry, re-reads the buckets; the termination lemma of Appendix A
 // bounds the retries by the slots involved.
-// When lookup_only is set the kernel is the Section 2.3 lookup instead.
+// With LOOKUP set the engine is the Section 2.3 lookup instead.
+//
+// The engine runs over a work source: one table (SingleWork) or a batch of
+// tables (BatchWork), which hands out chunks of keys together with the table
+// they belong to. The primary packing FPW0 is a template parameter; the
+// secondary level, visited only by keys whose primary bucket is full, reads
+// its packing at run time.
 // ===========================================================================
-// The primary packing FPW0 is a template parameter; the secondary level,
-// visited only by keys whose primary bucket is full, reads its packing at
-// run time.
-template <int T, int FPW0, bool LOOKUP>
-__global__ void __launch_bounds__(256)
-    k_iceberg(TableArgs ta, const void *__restrict__ keys, uint64_t n,
-              uint8_t *__restrict__ status, int items) {
+
+// work source over one table: TileWork plus the table's arguments
+template <int T>
+struct SingleWork : TileWork<T> {
+    const TableArgs *tap;
+    const void *keys;
+    uint64_t n;
+    uint8_t *status;
+    __device__ __forceinline__ const TableArgs &ta() const { return *tap; }
+    __device__ __forceinline__ void next() { this->refill(keys, tap->key_bytes, n, status); }
+};
+
+// one (table, keys, statuses) triple of a fused multi-table launch
+struct BatchDesc {
+    TableArgs ta;
+    const void *keys;
+    uint64_t n;
+    uint8_t *status;
+};
+
+// work source over many tables: the chunks of all tables form one index
+// space (table t owns chunks [prefix[t], prefix[t+1]) ), walked by every tile
+// with a grid stride; prefix lives in shared memory, computed by the block
+template <int T>
+struct BatchWork {
+    uint64_t *s_keys;
+    uint8_t *s_st;
+    const BatchDesc *bd;
+    const uint64_t *prefix;
+    int count, cur, items, q, qn;
+    uint64_t chunk, nchunks, stride, base;
+    bool done;
+
+    __device__ __forceinline__ void init(uint64_t *smem_keys, uint8_t *smem_st, int items_,
+                                         const BatchDesc *bd_, const uint64_t *prefix_,
+                                         int count_) {
+        const int tiles_per_block = blockDim.x / T;
+        const int tib = threadIdx.x / T;
+        items = items_;
+        s_keys = smem_keys + (size_t)tib * T * items;
+        s_st = smem_st + (size_t)tib * T * items;
+        bd = bd_;
+        prefix = prefix_;
+        count = count_;
+        nchunks = prefix[count];
+        stride = (uint64_t)gridDim.x * tiles_per_block;
+        chunk = (uint64_t)blockIdx.x * tiles_per_block + tib;
+        done = chunk >= nchunks;
+        cur = 0;
+        q = qn = 0;
+        base = 0;
+    }
+    __device__ __forceinline__ const TableArgs &ta() const { return bd[cur].ta; }
+    __device__ __forceinline__ void next() {
+        const int tl = threadIdx.x & (T - 1);
+        const uint64_t per = (uint64_t)T * items;
+        if (qn > 0) {
+            uint8_t *st = bd[cur].status;
+            for (int i = 0; i < items; ++i) {
+                int idx = i * T + tl;
+                if (idx < qn) st[base + idx] = s_st[idx];
+            }
+            chunk += stride;
+        }
+        if (chunk >= nchunks) {
+            done = true;
+            qn = q = 0;
+            return;
+        }
+        // table owning this chunk: the last t with prefix[t] <= chunk
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= chunk)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        cur = lo;
+        const BatchDesc &d = bd[cur];
+        base = (chunk - prefix[cur]) * per;
+        const uint64_t rem = d.n - base;
+        qn = rem < per ? (int)rem : (int)per;
+        q = 0;
+        for (int i = 0; i < items; ++i) {
+            int idx = i * T + tl;
+            if (idx < qn) s_keys[idx] = load_key(d.keys, d.ta.key_bytes, base + idx);
+        }
+    }
+};
+
+template <int T, int FPW0, bool LOOKUP, class Work>
+__device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr) {
     constexpr int W = kWordsPerBucket / T;
-    const int FPW1 = ta.lv[1].fpw;
-    const int LF1 = W * FPW1;
-    const int B1 = kWordsPerBucket * FPW1;
-    const int kMaxIter = 4 * (kWordsPerBucket * FPW0 + 2 * B1) + 16;
-    extern __shared__ uint64_t smem[];
-    TileWork<T> tw;
-    tw.init(smem, reinterpret_cast<uint8_t *>(smem + (size_t)blockDim.x * items), items, n,
-            ta.max_tiles);
     const int tl = threadIdx.x & (T - 1);
-    const Level &L0 = ta.lv[0];
-    const Level &L1 = ta.lv[1];
     uint64_t cur = 0;
     int lvl = 1, it = 0;
     bool fresh = true;
@@ -292,8 +374,14 @@ __global__ void __launch_bounds__(256)
     int n_fail = 0;
 
     while (__any_sync(0xffffffffu, !tw.done)) {
-        if (!tw.done && tw.q >= tw.qn) tw.refill(keys, ta.key_bytes, n, status);
+        if (!tw.done && tw.q >= tw.qn) tw.next();
         __syncwarp();
+        const TableArgs &ta = tw.ta();
+        const Level &L0 = ta.lv[0];
+        const Level &L1 = ta.lv[1];
+        const int FPW1 = L1.fpw;
+        const int LF1 = W * FPW1;
+        const int B1 = kWordsPerBucket * FPW1;
         const bool act = !tw.done;
         if (act && fresh) {
             cur = tw.s_keys[tw.q];
@@ -329,11 +417,10 @@ __global__ void __launch_bounds__(256)
         const uint32_t be0 = tile_ballot<T>(p1 && f0 >= 0);
         const uint32_t bea = tile_ballot<T>(p2 && fa >= 0);
         const uint32_t beb = tile_ballot<T>(p2 && fb >= 0);
-        // first empty slot index of each snapshot (B if none)
+        // first empty slot index of each snapshot (B1 if none)
         const int la0 = be0 ? __ffs(be0) - 1 : 0;
         const int laa = bea ? __ffs(bea) - 1 : 0;
         const int lab = beb ? __ffs(beb) - 1 : 0;
-        const int fe0 = tile_shfl<T>(f0, la0);
         const int fea = tile_shfl<T>(fa, laa);
         const int feb = tile_shfl<T>(fb, lab);
         const int loada = bea ? laa * LF1 + fea : B1;
@@ -393,9 +480,10 @@ __global__ void __launch_bounds__(256)
                     n_write++;
                 } else {
                     const uint64_t mine = (lvl == 1) ? e0 : (pick_a ? ea : eb);
+                    const int max_iter = 4 * (kWordsPerBucket * FPW0 + 2 * B1) + 16;
                     if (seen == mine) {
                         st = ST_FOUND;  // another thread inserted k first
-                    } else if (++it > kMaxIter) {
+                    } else if (++it > max_iter) {
                         st = ST_ERROR;
                     } else {
                         fin = false;  // re-read the bucket(s) at this level
@@ -414,13 +502,62 @@ __global__ void __launch_bounds__(256)
         }
         __syncwarp();
     }
-    if (ta.ctr) {
+    if (ctr) {
         if (tl != 0) n_probe = n_write = 0;
-        flush_counter(ta.ctr, 0, n_probe);
-        flush_counter(ta.ctr, 1, n_write);
-        flush_counter(ta.ctr, 2, (uint64_t)n_fail);
-        flush_counter(ta.ctr, 3, n_ops);
+        flush_counter(ctr, 0, n_probe);
+        flush_counter(ctr, 1, n_write);
+        flush_counter(ctr, 2, (uint64_t)n_fail);
+        flush_counter(ctr, 3, n_ops);
     }
+}
+
+template <int T, int FPW0, bool LOOKUP>
+__global__ void __launch_bounds__(256)
+    k_iceberg(TableArgs ta, const void *__restrict__ keys, uint64_t n,
+              uint8_t *__restrict__ status, int items) {
+    extern __shared__ uint64_t smem[];
+    SingleWork<T> tw;
+    tw.init(smem, reinterpret_cast<uint8_t *>(smem + (size_t)blockDim.x * items), items, n,
+            ta.max_tiles);
+    tw.tap = &ta;
+    tw.keys = keys;
+    tw.n = n;
+    tw.status = status;
+    iceberg_engine<T, FPW0, LOOKUP>(tw, ta.ctr);
+}
+
+// One persistent launch over many tables (a fused multi-table batch). Shared
+// memory: the chunk prefix of all tables, then the staged keys and statuses.
+template <int T, int FPW0, bool LOOKUP>
+__global__ void __launch_bounds__(256)
+    k_iceberg_batch(const BatchDesc *__restrict__ bd, int count, int items,
+                    unsigned long long *ctr) {
+    extern __shared__ uint64_t smem[];
+    uint64_t *prefix = smem;  // count + 1 entries
+    const uint64_t per = (uint64_t)T * items;
+    // chunk counts of every table, scanned by the first warp
+    if (threadIdx.x < 32) {
+        uint64_t carry = 0;
+        for (int b0 = 0; b0 < count; b0 += 32) {
+            const int t = b0 + (int)threadIdx.x;
+            uint64_t c = t < count ? (bd[t].n + per - 1) / per : 0;
+            uint64_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)threadIdx.x >= o) incl += y;
+            }
+            if (t < count) prefix[t] = carry + incl - c;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (threadIdx.x == 0) prefix[count] = carry;
+    }
+    __syncthreads();
+    uint64_t *keys = smem + ((count + 2) & ~1);
+    BatchWork<T> tw;
+    tw.init(keys, reinterpret_cast<uint8_t *>(keys + (size_t)blockDim.x * items), items, bd,
+            prefix, count);
+    iceberg_engine<T, FPW0, LOOKUP>(tw, ctr);
 }
 
 }  // namespace cht

@@ -74,4 +74,9 @@ cudaError_t launch_cuckoo_find(int T, int fpw, const LaunchParams &lp, const Tab
 cudaError_t launch_iceberg(int T, int fpw0, bool lookup, const LaunchParams &lp,
                            const TableArgs &ta, const void *keys, uint64_t n, uint8_t *status);
 
+struct BatchDesc;
+cudaError_t launch_iceberg_batch(int T, int fpw0, bool lookup, const LaunchParams &lp,
+                                 const BatchDesc *bd, int count, uint64_t total_chunks,
+                                 unsigned long long *ctr);
+
 }  // namespace cht

@@ -2,7 +2,7 @@
 // stored key) and clear. Included by the C ABI unit only.
 #pragma once
 
-#include "cht_device.cuh"
+#include "cht_kernels.cuh"
 
 namespace cht {
 
@@ -76,6 +76,20 @@ __global__ void __launch_bounds__(256)
 
 __global__ void k_zero_u64(unsigned long long *p) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *p = 0ull;
+}
+
+// zero the storage (header and both levels) of every table of a batch: the
+// whole grid sweeps one table after another
+__global__ void __launch_bounds__(256) k_clear_batch(const BatchDesc *__restrict__ bd, int count) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (int t = 0; t < count; ++t) {
+        const TableArgs &ta = bd[t].ta;
+        ulonglong2 *p = reinterpret_cast<ulonglong2 *>(ta.err);  // header start
+        const uint64_t nb = ta.lv[0].nb + ta.lv[1].nb;  // lv[1].nb is 0 for cuckoo
+        const uint64_t n16 = (256 + nb * 128) / 16;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride)
+            __stcs(p + i, make_ulonglong2(0ull, 0ull));
+    }
 }
 
 // zero n16 16-byte units starting at p (16-byte aligned)

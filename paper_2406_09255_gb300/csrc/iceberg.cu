@@ -42,3 +42,50 @@ cudaError_t launch_iceberg(int T, int fpw0, bool lookup, const LaunchParams &lp,
 }
 
 }  // namespace cht
+
+namespace cht {
+
+template <int T, int FPW0, bool LOOKUP>
+static cudaError_t run_batch(const LaunchParams &lp, const BatchDesc *bd, int count,
+                             uint64_t total_chunks, unsigned long long *ctr) {
+    auto kern = k_iceberg_batch<T, FPW0, LOOKUP>;
+    const size_t smem = (size_t)((count + 2) & ~1) * 8 + smem_bytes(lp.cta, lp.items);
+    const uint64_t tiles_per_block = lp.cta / T;
+    uint64_t need = (total_chunks + tiles_per_block - 1) / tiles_per_block;
+    uint64_t cap = (uint64_t)lp.sms * occupancy((const void *)kern, lp.cta, smem);
+    if (lp.max_ctas > 0 && cap > (uint64_t)lp.max_ctas) cap = lp.max_ctas;
+    int blocks = (int)(need < cap ? need : cap);
+    if (blocks < 1) blocks = 1;
+    kern<<<blocks, lp.cta, smem, lp.stream>>>(bd, count, lp.items, ctr);
+    return cudaGetLastError();
+}
+
+template <int T>
+static cudaError_t batch_by_fpw(int fpw0, bool lookup, const LaunchParams &lp,
+                                const BatchDesc *bd, int count, uint64_t total_chunks,
+                                unsigned long long *ctr) {
+    switch (fpw0) {
+        case 1: return lookup ? run_batch<T, 1, true>(lp, bd, count, total_chunks, ctr)
+                              : run_batch<T, 1, false>(lp, bd, count, total_chunks, ctr);
+        case 2: return lookup ? run_batch<T, 2, true>(lp, bd, count, total_chunks, ctr)
+                              : run_batch<T, 2, false>(lp, bd, count, total_chunks, ctr);
+        case 3: return lookup ? run_batch<T, 3, true>(lp, bd, count, total_chunks, ctr)
+                              : run_batch<T, 3, false>(lp, bd, count, total_chunks, ctr);
+        case 4: return lookup ? run_batch<T, 4, true>(lp, bd, count, total_chunks, ctr)
+                              : run_batch<T, 4, false>(lp, bd, count, total_chunks, ctr);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_iceberg_batch(int T, int fpw0, bool lookup, const LaunchParams &lp,
+                                 const BatchDesc *bd, int count, uint64_t total_chunks,
+                                 unsigned long long *ctr) {
+    switch (T) {
+        case 4: return batch_by_fpw<4>(fpw0, lookup, lp, bd, count, total_chunks, ctr);
+        case 8: return batch_by_fpw<8>(fpw0, lookup, lp, bd, count, total_chunks, ctr);
+        case 16: return batch_by_fpw<16>(fpw0, lookup, lp, bd, count, total_chunks, ctr);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cht

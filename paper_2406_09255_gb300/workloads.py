@@ -278,3 +278,27 @@ def poisson_arrivals(n: int, rate_per_s: float, rng_seed: int) -> np.ndarray:
     """Arrival times (seconds) of a Poisson process of the given rate."""
     rng = np.random.default_rng(rng_seed)
     return np.cumsum(rng.exponential(1.0 / rate_per_s, n))
+
+
+def multi_table_spec(count: int = 256, lo_exp: int = 8, hi_exp: int = 18,
+                     min_batch: int = 1000, max_batch: int = 1_000_000,
+                     distinct_frac: float = 0.7, slots_per_primary: int = 32,
+                     slots_per_backyard: int = 32, fill_cap: float = 0.85,
+                     rng_seed: int = SEED_BASE + 4):
+    """Shape of a many-table find-or-put workload.
+
+    Table i has 2^e_i primary buckets (e_i uniform in [lo_exp, hi_exp]) and
+    2^(e_i - 3) secondary buckets, and receives one batch whose size is
+    log-uniform in [min_batch, max_batch], capped so that its distinct keys
+    (distinct_frac of the batch) stay below fill_cap of the table's slots.
+    Returns a list of (primary_exp, batch_size, distinct) tuples."""
+    rng = np.random.default_rng(rng_seed)
+    exps = rng.integers(lo_exp, hi_exp + 1, count)
+    sizes = log_uniform_sizes(count, min_batch, max_batch, rng_seed + 1)
+    out = []
+    for e, s in zip(exps, sizes):
+        slots = (1 << int(e)) * slots_per_primary + (1 << (int(e) - 3)) * slots_per_backyard
+        cap = int(fill_cap * slots / distinct_frac)
+        s = int(min(s, cap))
+        out.append((int(e), s, int(distinct_frac * s)))
+    return out

@@ -1,0 +1,162 @@
+"""Fused multi-table batches (one persistent launch over many iceberg tables,
+plain or replayed from a CUDA graph) against the per-table contract and the
+oracle: for every table of the batch, exactly one PUT per distinct key, the
+stored set equal to the oracle's, a well-formed table (Theorem 1 (a)), and
+lookups that equal membership."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2406_09255_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0) if torch.cuda.is_available() else None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def P():
+    import paper_2406_09255_gb300 as m
+    return m
+
+
+def mirror(t):
+    c = t.cfg
+    return oracle.Table(c.kind, c.key_bits, c.num_buckets, c.num_buckets_backyard,
+                        compact=bool(c.compact), fpw0=c.fields_per_word,
+                        fpw1=c.fields_per_word_backyard, seed=c.seed)
+
+
+def dump(t):
+    o = mirror(t)
+    o.load_words(t.words(0).cpu().numpy().view(np.uint64),
+                 t.words(1).cpu().numpy().view(np.uint64))
+    return o
+
+
+def u64(x):
+    a = x.detach().cpu().numpy()
+    return a.view(np.uint32).astype(np.uint64) if a.dtype == np.int32 else a.view(np.uint64)
+
+
+def make_tables(spec, key_bits=32, seed0=100):
+    m = P()
+    tables, keys = [], []
+    for i, (e, size, distinct) in enumerate(spec):
+        t = m.Table(m.ICEBERG, key_bits, 1 << e, 1 << (e - 3), key_bytes=4, fields_per_word=2,
+                    seed=seed0 + i)
+        k = W.duplicate_stream(size, distinct, key_bits, seed0 + 7 * i, 0.3)
+        tables.append(t)
+        keys.append(W.to_u32(k).to(DEV))
+    return tables, keys
+
+
+SPEC = [(8, 5000, 3500), (12, 100000, 70000), (9, 1, 1), (10, 20000, 14000), (14, 300000, 210000),
+        (8, 1000, 700), (11, 0, 0), (13, 77777, 54443)]
+
+
+def check_table(t, k, st):
+    m = P()
+    kn = u64(k)
+    st = st.cpu().numpy()
+    o = mirror(t)
+    ost = o.insert(kn) if len(kn) else np.zeros(0, np.uint8)
+    assert (ost != oracle.FULL).all()
+    assert ((st == m.PUT) | (st == m.FOUND)).all()
+    if len(kn):
+        uniq, inv = np.unique(kn, return_inverse=True)
+        puts = np.bincount(inv, weights=(st == m.PUT), minlength=len(uniq))
+        assert (puts == 1).all()
+    stored, cnt = t.enumerate()
+    assert np.array_equal(np.sort(u64(stored)), np.sort(o.enumerate()))
+    d = dump(t)
+    assert d.check_entries() == 0 and d.check_order_property() == 0 and d.check_prefix() == 0
+
+
+@pytest.mark.parametrize("tile,items", [(4, 2), (8, 1), (16, 8)])
+def test_fused_batch_find_or_put(tile, items):
+    m = P()
+    from paper_2406_09255_gb300.batch import Batch, OP_FIND
+    tables, keys = make_tables(SPEC)
+    b = Batch(tables, keys)
+    b.set_launch(tile=tile, items_per_thread=items)
+    sts = b.launch()
+    torch.cuda.synchronize()
+    for t, k, s in zip(tables, keys, sts):
+        check_table(t, k, s)
+        assert t.error_flags() == 0
+    # lookups of all keys plus absent ones, fused, are exact membership
+    qk = [torch.cat([k, W.to_u32(W.unique_keys(10**6, 500, 32, 999 + i)).to(DEV)])
+          for i, k in enumerate(keys)]
+    bf = Batch(tables, qk, op=OP_FIND)
+    fs = bf.launch()
+    for t, q, s in zip(tables, qk, fs):
+        stored = set(u64(t.enumerate()[0]).tolist())
+        want = np.array([int(x) in stored for x in u64(q)])
+        assert np.array_equal(s.cpu().numpy() == m.FOUND, want)
+
+
+def test_graph_replay_matches_and_repeats():
+    m = P()
+    from paper_2406_09255_gb300.batch import Batch
+    tables, keys = make_tables(SPEC, seed0=300)
+    b = Batch(tables, keys)
+    b.capture()
+    for rep in range(2):
+        b.clear()
+        sts = b.replay()
+        torch.cuda.synchronize()
+        for t, k, s in zip(tables, keys, sts):
+            check_table(t, k, s)
+    # replay without clearing: everything is already there
+    sts = b.replay()
+    for s in sts:
+        assert (s.cpu().numpy() == m.FOUND).all()
+
+
+def test_fused_equals_per_table_sets():
+    from paper_2406_09255_gb300.batch import Batch, per_table
+    tables, keys = make_tables(SPEC, seed0=500)
+    tables2, _ = make_tables(SPEC, seed0=500)
+    b = Batch(tables, keys)
+    b.launch()
+    st2 = [torch.empty(k.numel(), dtype=torch.uint8, device=DEV) for k in keys]
+    per_table(tables2, keys, st2)
+    for t1, t2, s1, s2 in zip(tables, tables2, b.statuses, st2):
+        assert np.array_equal(np.sort(u64(t1.enumerate()[0])), np.sort(u64(t2.enumerate()[0])))
+        # the same number of PUTs (one per distinct key) on both paths
+        assert int((s1 == 2).sum()) == int((s2 == 2).sum())
+
+
+def test_batch_rejects_mixed_packing_and_cuckoo():
+    m = P()
+    from paper_2406_09255_gb300.batch import Batch
+    a = m.Table(m.ICEBERG, 32, 1 << 8, 1 << 5, key_bytes=4, fields_per_word=2, seed=1)
+    b = m.Table(m.ICEBERG, 32, 1 << 8, 1 << 5, key_bytes=4, fields_per_word=1, seed=1)
+    c = m.Table(m.CUCKOO, 32, 1 << 8, key_bytes=4, seed=1)
+    k = torch.ones(4, dtype=torch.int32, device=DEV)
+    with pytest.raises(m.ChtError):
+        Batch([a, b], [k, k])
+    with pytest.raises(m.ChtError):
+        Batch([a, c], [k, k])
+
+
+def test_tuner_picks_a_valid_shape(tmp_path, monkeypatch):
+    monkeypatch.setenv("CHT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    from paper_2406_09255_gb300.batch import Batch
+    from paper_2406_09255_gb300.tune import tune_batch
+    tables, keys = make_tables(SPEC[:4], seed0=700)
+    b = Batch(tables, keys)
+    r = tune_batch(b, reps=1, tiles=(4, 8), items=(1, 2))
+    assert r["tile"] in (4, 8) and r["items"] in (1, 2) and not r["cached"]
+    # the tuner restored the empty tables: a launch now inserts everything
+    sts = b.launch()
+    for t, k, s in zip(tables, keys, sts):
+        check_table(t, k, s)
+    r2 = tune_batch(b, reps=1)
+    assert r2["cached"] and r2["tile"] == r["tile"]
