@@ -286,6 +286,35 @@ int cht_batch_clear(const cht_batch *b, void *stream);
 /* Free the batch handle and its graph (the scratch stays the caller's). */
 int cht_batch_destroy(cht_batch *b);
 
+/*
+ * Allocation-free fused find-or-put (the paper has no counterpart; this is a
+ * convenience of this library). Same work as cht_batch_create with
+ * CHT_OP_FIND_OR_PUT followed by cht_batch_launch, but for callers that must
+ * not allocate device memory at all: code that runs while another thread
+ * captures a CUDA graph in global capture mode (where cudaMalloc is an illegal
+ * call), latency-critical loops that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause, and hosts where another
+ * allocator has already reserved the GPU's memory so a fresh cudaMalloc fails.
+ *
+ * The batch descriptors live in a fixed array inside the library (device
+ * memory that every GPU which loads the library holds until the process
+ * exits) with room for CHT_STATIC_BATCH_MAX tables; count above that is
+ * rejected with CHT_ERR_INVALID. Nothing is allocated on any call: the
+ * descriptors are written into the array by a copy on stream, then the fused
+ * kernel runs. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call shares the one array and each call
+ * overwrites the descriptors it uses (nothing in it has to start at zero), so
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race: order them on one stream. Arguments and per-key results are
+ * as for cht_batch_create / cht_find_or_put; all tables must be iceberg tables
+ * with the same primary packing on the current device.
+ */
+#define CHT_STATIC_BATCH_MAX 256
+int cht_batch_find_or_put_static(cht_table *const *tables, const void *const *d_keys,
+                                 const size_t *n, uint8_t *const *d_status, int count,
+                                 void *stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *cht_last_error(void);
 

@@ -79,6 +79,9 @@ SIGNATURES = {
     "cht_batch_replay": (ctypes.c_int, [_vp, _vp]),
     "cht_batch_clear": (ctypes.c_int, [_vp, _vp]),
     "cht_batch_destroy": (ctypes.c_int, [_vp]),
+    "cht_batch_find_or_put_static": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                                    ctypes.POINTER(ctypes.c_size_t),
+                                                    ctypes.POINTER(_vp), ctypes.c_int, _vp]),
     "cht_last_error": (ctypes.c_char_p, []),
     "cht_version": (ctypes.c_char_p, []),
 }

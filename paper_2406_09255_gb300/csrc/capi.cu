@@ -592,3 +592,93 @@ int cht_batch_destroy(cht_batch *b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free fused find-or-put: the batch descriptors live in a fixed
+// array of this library instead of caller scratch (the paper has no
+// counterpart; see the declaration in cht.h for who needs it).
+// ---------------------------------------------------------------------------
+namespace {
+
+// room for CHT_STATIC_BATCH_MAX descriptors; held by every GPU that loads the
+// library until the process exits
+static __device__ __align__(256) unsigned char
+    g_static_batch[CHT_STATIC_BATCH_MAX * sizeof(BatchDesc)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices];  // device address of g_static_batch, per device
+
+// the array's device address on device dev (current): looked up on the first
+// call on that device, then reused
+int static_batch_address(int dev, void **out) {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t ce = cudaGetSymbolAddress(&p, g_static_batch);
+        if (ce != cudaSuccess) return cuda_fail(ce, "looking up the static batch array");
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return CHT_OK;
+}
+
+}  // namespace
+
+extern "C" int cht_batch_find_or_put_static(cht_table *const *tables, const void *const *d_keys,
+                                            const size_t *n, uint8_t *const *d_status, int count,
+                                            void *stream) {
+    if (!tables || !d_keys || !n || !d_status) return fail(CHT_ERR_INVALID, "null batch array");
+    if (count < 1 || count > CHT_STATIC_BATCH_MAX)
+        return fail(CHT_ERR_INVALID,
+                    "count = %d: the allocation-free batch takes 1..%d tables (its fixed array "
+                    "holds %d descriptors)",
+                    count, CHT_STATIC_BATCH_MAX, CHT_STATIC_BATCH_MAX);
+    int cur = -1;
+    cudaError_t ce = cudaGetDevice(&cur);
+    if (ce != cudaSuccess) return cuda_fail(ce, "device query");
+    if (cur < 0 || cur >= kMaxDevices) return fail(CHT_ERR_UNSUPPORTED, "device id %d", cur);
+    // descriptors are built on the stack (80 KB at most): no allocation
+    BatchDesc host[CHT_STATIC_BATCH_MAX];
+    int fpw0 = 0, sms = 0;
+    uint64_t total_chunks = 0;
+    const int T = 4, items = 2;
+    const uint64_t per = (uint64_t)T * items;
+    for (int i = 0; i < count; ++i) {
+        const cht_table *t = tables[i];
+        if (!t) return fail(CHT_ERR_INVALID, "null table at batch entry %d", i);
+        if (t->cfg.kind != CHT_ICEBERG)
+            return fail(CHT_ERR_UNSUPPORTED, "batch entry %d is not an iceberg table", i);
+        if (t->device != cur)
+            return fail(CHT_ERR_INVALID, "batch entry %d is not on the current device", i);
+        if (i == 0) {
+            fpw0 = t->cfg.fields_per_word;
+            sms = t->sms;
+        } else if (t->cfg.fields_per_word != fpw0) {
+            return fail(CHT_ERR_UNSUPPORTED, "batch entry %d differs in primary packing", i);
+        }
+        if (n[i] && (!d_keys[i] || !d_status[i]))
+            return fail(CHT_ERR_INVALID, "null keys or statuses at batch entry %d", i);
+        if ((uintptr_t)d_keys[i] % t->cfg.key_bytes)
+            return fail(CHT_ERR_INVALID, "keys of batch entry %d not aligned", i);
+        host[i].ta = t->args;
+        host[i].ta.max_tiles = 0;
+        host[i].ta.ctr = nullptr;
+        host[i].keys = d_keys[i];
+        host[i].n = n[i];
+        host[i].status = d_status[i];
+        total_chunks += (n[i] + per - 1) / per;
+    }
+    void *dst = nullptr;
+    int e = static_batch_address(cur, &dst);
+    if (e) return e;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // a copy from pageable memory returns once the source has been consumed,
+    // so the stack copy may go out of scope right after
+    ce = cudaMemcpyAsync(dst, host, sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "writing the static batch descriptors");
+    if (total_chunks == 0) return ok();
+    ce = launch_iceberg_batch_noalloc(fpw0, s, sms, static_cast<const BatchDesc *>(dst), count,
+                                      total_chunks);
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "static batch kernel launch");
+}

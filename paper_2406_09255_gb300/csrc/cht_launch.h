@@ -78,5 +78,7 @@ struct BatchDesc;
 cudaError_t launch_iceberg_batch(int T, int fpw0, bool lookup, const LaunchParams &lp,
                                  const BatchDesc *bd, int count, uint64_t total_chunks,
                                  unsigned long long *ctr);
+cudaError_t launch_iceberg_batch_noalloc(int fpw0, cudaStream_t s, int sms, const BatchDesc *bd,
+                                         int count, uint64_t total_chunks);
 
 }  // namespace cht

@@ -89,3 +89,38 @@ cudaError_t launch_iceberg_batch(int T, int fpw0, bool lookup, const LaunchParam
 }
 
 }  // namespace cht
+
+namespace cht {
+
+// fused find-or-put launch that allocates nothing on the host either: the
+// grid comes from a direct occupancy query instead of the cached one
+template <int FPW0>
+static cudaError_t run_batch_noalloc(cudaStream_t s, int sms, const BatchDesc *bd, int count,
+                                     uint64_t total_chunks) {
+    constexpr int T = 4, kItems = 2, kCta = 256;
+    auto kern = k_iceberg_batch<T, FPW0, false>;
+    const size_t smem = (size_t)((count + 2) & ~1) * 8 + smem_bytes(kCta, kItems);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kCta, smem) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    const uint64_t need = (total_chunks + kCta / T - 1) / (kCta / T);
+    const uint64_t cap = (uint64_t)sms * occ;
+    int blocks = (int)(need < cap ? need : cap);
+    if (blocks < 1) blocks = 1;
+    kern<<<blocks, kCta, smem, s>>>(bd, count, kItems, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iceberg_batch_noalloc(int fpw0, cudaStream_t s, int sms, const BatchDesc *bd,
+                                         int count, uint64_t total_chunks) {
+    switch (fpw0) {
+        case 1: return run_batch_noalloc<1>(s, sms, bd, count, total_chunks);
+        case 2: return run_batch_noalloc<2>(s, sms, bd, count, total_chunks);
+        case 3: return run_batch_noalloc<3>(s, sms, bd, count, total_chunks);
+        case 4: return run_batch_noalloc<4>(s, sms, bd, count, total_chunks);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cht
