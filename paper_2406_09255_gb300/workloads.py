@@ -269,6 +269,36 @@ def zipf_recency_stream(n_ops: int, key_bits: int, seed: int, *,
     return idx.astype(np.int64), is_find, int(fop_fresh.sum())
 
 
+def fop_stream(n_ops: int, key_bits: int, seed: int, *, fresh_frac: float = 0.5,
+               zipf_s: float = 0.99, find_frac: float = 0.2, max_distinct: int | None = None,
+               rng_seed: int = 0, device="cpu"):
+    """The same model-checking-like stream as zipf_recency_stream, generated
+    with torch on `device` (for streams of hundreds of millions of ops).
+
+    Returns (keys int64, is_find bool, fresh_before int64): fresh_before[i] is
+    the number of distinct keys introduced by find-or-puts before op i."""
+    g = torch.Generator(device=device)
+    g.manual_seed(rng_seed)
+    is_find = torch.rand(n_ops, generator=g, device=device) < find_frac
+    is_fresh = torch.rand(n_ops, generator=g, device=device) < fresh_frac
+    fop_fresh = is_fresh & ~is_find
+    counter = torch.cumsum(fop_fresh.to(torch.int64), 0) - fop_fresh.to(torch.int64)
+    if max_distinct is not None:
+        fop_fresh &= counter < max_distinct
+        counter.clamp_(max=max_distinct)
+    n_seen = counter  # keys introduced before this op
+    u = torch.rand(n_ops, generator=g, device=device, dtype=torch.float64)
+    a = 1.0 - zipf_s
+    cap = n_seen.clamp(min=1).to(torch.float64)
+    rank = torch.floor(((cap ** a - 1.0) * u + 1.0) ** (1.0 / a)).to(torch.int64)
+    rank = torch.minimum(rank.clamp(min=1), n_seen.clamp(min=1))
+    idx = torch.where(fop_fresh, counter, n_seen - rank)
+    absent_base = 1 << (key_bits - 2)
+    miss = (is_fresh & is_find) | ((~fop_fresh) & (n_seen == 0))
+    idx = torch.where(miss, absent_base + torch.arange(n_ops, device=device), idx)
+    return keys_at(idx, key_bits, seed), is_find, counter
+
+
 def log_uniform_sizes(n: int, lo: int, hi: int, rng_seed: int) -> np.ndarray:
     rng = np.random.default_rng(rng_seed)
     return np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi + 1), n))).astype(np.int64).clip(lo, hi)
