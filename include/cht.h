@@ -87,9 +87,11 @@ typedef struct cht_table cht_table; /* opaque host handle */
  *                       (Algorithm 4); 0 = 128.
  * seed                  all permutation constants derive from it.
  * tile                  threads cooperating on one bucket: 4, 8 or 16; 0 lets
- *                       each operation use its fastest width (lookups 8,
- *                       puts and find-or-puts 4).
- * items_per_thread      keys each thread loads per work chunk, 1..8 (0 = 2).
+ *                       each operation use its fastest width (cuckoo puts 4,
+ *                       everything else 8).
+ * items_per_thread      keys each thread holds per work chunk, 1..8 (0 = 2);
+ *                       iceberg operations use 1, 2 or 4 (larger values
+ *                       count as 4, 3 as 2).
  * cta_threads           threads per block, a multiple of 32 (0 = 256).
  * max_ctas              upper bound on blocks (0 = enough to fill the GPU).
  * max_tiles             upper bound on tiles that take work (0 = no bound).
@@ -258,7 +260,7 @@ size_t cht_batch_scratch_bytes(int count);
  * d_status[i]). The descriptors are written into the caller-owned device
  * scratch d_scratch (at least cht_batch_scratch_bytes(count) bytes, 16-byte
  * aligned) by a copy enqueued on stream; the scratch must stay untouched until
- * cht_batch_destroy. Launch shape: tile 4, 2 items per thread, 256 threads
+ * cht_batch_destroy. Launch shape: tile 8, 1 item per thread, 256 threads
  * per block unless changed with cht_batch_set_launch.
  */
 int cht_batch_create(cht_table *const *tables, const void *const *d_keys, const size_t *n,

@@ -170,7 +170,7 @@ int tile_for(const cht_table *t, Op op) {
     switch (op) {
         case kOpCuckooInsert: return 4;
         case kOpCuckooFind: return 8;
-        case kOpIcebergFop: return 4;
+        case kOpIcebergFop: return 8;
         case kOpIcebergFind: return 8;
     }
     return 8;
@@ -410,14 +410,14 @@ namespace {
 int batch_launch_params(const cht_batch *b, void *stream, LaunchParams &lp, int &T,
                         uint64_t &chunks) {
     lp.cta = b->launch.cta_threads ? b->launch.cta_threads : 256;
-    lp.items = b->launch.items_per_thread ? b->launch.items_per_thread : 2;
+    lp.items = b->launch.items_per_thread ? b->launch.items_per_thread : 1;
     lp.max_ctas = b->launch.max_ctas;
     lp.max_tiles = 0;
     lp.in_flight = 1;
     lp.sms = b->sms;
     lp.stream = static_cast<cudaStream_t>(stream);
-    T = b->launch.tile ? b->launch.tile : 4;
-    const uint64_t per = (uint64_t)T * lp.items;
+    T = b->launch.tile ? b->launch.tile : 8;
+    const uint64_t per = (uint64_t)32 * batch_items(lp.items);
     chunks = 0;
     for (const BatchDesc &d : b->host) chunks += (d.n + per - 1) / per;
     return CHT_OK;
@@ -642,8 +642,7 @@ extern "C" int cht_batch_find_or_put_static(cht_table *const *tables, const void
     BatchDesc host[CHT_STATIC_BATCH_MAX];
     int fpw0 = 0, sms = 0;
     uint64_t total_chunks = 0;
-    const int T = 4, items = 2;
-    const uint64_t per = (uint64_t)T * items;
+    const uint64_t per = (uint64_t)32 * kStaticBatchItems;
     for (int i = 0; i < count; ++i) {
         const cht_table *t = tables[i];
         if (!t) return fail(CHT_ERR_INVALID, "null table at batch entry %d", i);

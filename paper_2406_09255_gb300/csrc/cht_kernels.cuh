@@ -266,9 +266,10 @@ __global__ void __launch_bounds__(256, U == 1 ? 6 : (U == 2 ? 5 : 4))
 // bounds the retries by the slots involved.
 // With LOOKUP set the engine is the Section 2.3 lookup instead.
 //
-// The engine runs over a work source: one table (SingleWork) or a batch of
-// tables (BatchWork), which hands out chunks of keys together with the table
-// they belong to. The primary packing FPW0 is a template parameter; the
+// This engine processes each tile's keys strictly in input order; it serves
+// runs with a bounded number of tiles (max_tiles > 0, e.g. the sequential
+// single-tile run). Unordered runs use the warp-batched engine of
+// cht_warp.cuh. The primary packing FPW0 is a template parameter; the
 // secondary level, visited only by keys whose primary bucket is full, reads
 // its packing at run time.
 // ===========================================================================
@@ -290,77 +291,6 @@ struct BatchDesc {
     const void *keys;
     uint64_t n;
     uint8_t *status;
-};
-
-// work source over many tables: the chunks of all tables form one index
-// space (table t owns chunks [prefix[t], prefix[t+1]) ), walked by every tile
-// with a grid stride; prefix lives in shared memory, computed by the block
-template <int T>
-struct BatchWork {
-    uint64_t *s_keys;
-    uint8_t *s_st;
-    const BatchDesc *bd;
-    const uint64_t *prefix;
-    int count, cur, items, q, qn;
-    uint64_t chunk, nchunks, stride, base;
-    bool done;
-
-    __device__ __forceinline__ void init(uint64_t *smem_keys, uint8_t *smem_st, int items_,
-                                         const BatchDesc *bd_, const uint64_t *prefix_,
-                                         int count_) {
-        const int tiles_per_block = blockDim.x / T;
-        const int tib = threadIdx.x / T;
-        items = items_;
-        s_keys = smem_keys + (size_t)tib * T * items;
-        s_st = smem_st + (size_t)tib * T * items;
-        bd = bd_;
-        prefix = prefix_;
-        count = count_;
-        nchunks = prefix[count];
-        stride = (uint64_t)gridDim.x * tiles_per_block;
-        chunk = (uint64_t)blockIdx.x * tiles_per_block + tib;
-        done = chunk >= nchunks;
-        cur = 0;
-        q = qn = 0;
-        base = 0;
-    }
-    __device__ __forceinline__ const TableArgs &ta() const { return bd[cur].ta; }
-    __device__ __forceinline__ void next() {
-        const int tl = threadIdx.x & (T - 1);
-        const uint64_t per = (uint64_t)T * items;
-        if (qn > 0) {
-            uint8_t *st = bd[cur].status;
-            for (int i = 0; i < items; ++i) {
-                int idx = i * T + tl;
-                if (idx < qn) st[base + idx] = s_st[idx];
-            }
-            chunk += stride;
-        }
-        if (chunk >= nchunks) {
-            done = true;
-            qn = q = 0;
-            return;
-        }
-        // table owning this chunk: the last t with prefix[t] <= chunk
-        int lo = 0, hi = count - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (prefix[mid] <= chunk)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        cur = lo;
-        const BatchDesc &d = bd[cur];
-        base = (chunk - prefix[cur]) * per;
-        const uint64_t rem = d.n - base;
-        qn = rem < per ? (int)rem : (int)per;
-        q = 0;
-        for (int i = 0; i < items; ++i) {
-            int idx = i * T + tl;
-            if (idx < qn) s_keys[idx] = load_key(d.keys, d.ta.key_bytes, base + idx);
-        }
-    }
 };
 
 template <int T, int FPW0, bool LOOKUP, class Work>
@@ -524,40 +454,6 @@ __global__ void __launch_bounds__(256)
     tw.n = n;
     tw.status = status;
     iceberg_engine<T, FPW0, LOOKUP>(tw, ta.ctr);
-}
-
-// One persistent launch over many tables (a fused multi-table batch). Shared
-// memory: the chunk prefix of all tables, then the staged keys and statuses.
-template <int T, int FPW0, bool LOOKUP>
-__global__ void __launch_bounds__(256)
-    k_iceberg_batch(const BatchDesc *__restrict__ bd, int count, int items,
-                    unsigned long long *ctr) {
-    extern __shared__ uint64_t smem[];
-    uint64_t *prefix = smem;  // count + 1 entries
-    const uint64_t per = (uint64_t)T * items;
-    // chunk counts of every table, scanned by the first warp
-    if (threadIdx.x < 32) {
-        uint64_t carry = 0;
-        for (int b0 = 0; b0 < count; b0 += 32) {
-            const int t = b0 + (int)threadIdx.x;
-            uint64_t c = t < count ? (bd[t].n + per - 1) / per : 0;
-            uint64_t incl = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((int)threadIdx.x >= o) incl += y;
-            }
-            if (t < count) prefix[t] = carry + incl - c;
-            carry += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        if (threadIdx.x == 0) prefix[count] = carry;
-    }
-    __syncthreads();
-    uint64_t *keys = smem + ((count + 2) & ~1);
-    BatchWork<T> tw;
-    tw.init(keys, reinterpret_cast<uint8_t *>(keys + (size_t)blockDim.x * items), items, bd,
-            prefix, count);
-    iceberg_engine<T, FPW0, LOOKUP>(tw, ctr);
 }
 
 }  // namespace cht

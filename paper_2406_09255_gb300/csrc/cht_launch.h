@@ -73,8 +73,17 @@ cudaError_t launch_cuckoo_find(int T, int fpw, const LaunchParams &lp, const Tab
                                const void *keys, uint64_t n, uint8_t *status);
 cudaError_t launch_iceberg(int T, int fpw0, bool lookup, const LaunchParams &lp,
                            const TableArgs &ta, const void *keys, uint64_t n, uint8_t *status);
+cudaError_t launch_iceberg_warp(int T, int fpw0, bool lookup, const LaunchParams &lp,
+                                const TableArgs &ta, const void *keys, uint64_t n,
+                                uint8_t *status);
 
 struct BatchDesc;
+// launch shape of the allocation-free fused find-or-put
+constexpr int kStaticBatchTile = 8;
+constexpr int kStaticBatchItems = 1;
+// keys per lane of the warp-batched engine for an items_per_thread setting:
+// 1, 2 or 4 (a warp takes chunks of 32 * I keys of one table)
+inline int batch_items(int items) { return items >= 4 ? 4 : (items >= 2 ? 2 : 1); }
 cudaError_t launch_iceberg_batch(int T, int fpw0, bool lookup, const LaunchParams &lp,
                                  const BatchDesc *bd, int count, uint64_t total_chunks,
                                  unsigned long long *ctr);

@@ -1,0 +1,366 @@
+// cht_warp.cuh - warp-batched iceberg find-or-put and lookup (Algorithm 1,
+// Section 2.3) for unordered runs: the work sharing of Algorithm 3 with the
+// per-key arithmetic taken out of the tile.
+//
+// A warp takes chunks of 32 * I keys (I = items per lane). Every lane holds I
+// keys and computes their primary address and entry itself, once. Tiles of T
+// lanes then walk the pending keys of their own lanes in passes: a level-1
+// pass probes the primary bucket of every key still at level 1 (claiming its
+// first empty slot, Algorithm 1 lines for level 1), a level-2 pass probes both
+// secondary buckets of every key at level 2 (the secondary addresses are
+// computed only for keys that get there). In one round a tile takes the next
+// pending key of each of its I item slots, broadcasts their addresses
+// (Shuffle), issues the I bucket loads back to back, and answers each with
+// ballots (Any match, First empty); the lane owning the first empty slot does
+// the compare-and-swap and broadcasts the outcome to the key's lane. A key
+// whose claim lost a race is retried in the next pass at the same level, so
+// each key still follows Algorithm 1 step by step; keys of different lanes
+// interleave freely, as concurrent find-or-puts do.
+#pragma once
+
+#include <type_traits>
+
+#include "cht_kernels.cuh"
+
+namespace cht {
+
+// a warp's share of the keys: up to 32 * I keys of one table
+struct WarpChunk {
+    const TableArgs *ta;
+    const void *keys;
+    uint8_t *status;
+    uint64_t base;
+    int count;
+};
+
+// chunks of one table
+struct SingleSource {
+    const TableArgs *ta;
+    const void *keys;
+    uint8_t *status;
+    uint64_t n;
+    uint64_t per;  // keys per chunk
+    __device__ __forceinline__ uint64_t nchunks() const { return (n + per - 1) / per; }
+    __device__ __forceinline__ WarpChunk get(uint64_t c) const {
+        const uint64_t base = c * per;
+        const uint64_t rem = n - base;
+        return {ta, keys, status, base, (int)(rem < per ? rem : per)};
+    }
+};
+
+// chunks of many tables: table t owns chunks [prefix[t], prefix[t+1])
+struct BatchSource {
+    const BatchDesc *bd;
+    const uint64_t *prefix;
+    int count;
+    uint64_t per;
+    __device__ __forceinline__ uint64_t nchunks() const { return prefix[count]; }
+    __device__ __forceinline__ WarpChunk get(uint64_t c) const {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= c)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const BatchDesc &d = bd[lo];
+        const uint64_t base = (c - prefix[lo]) * per;
+        const uint64_t rem = d.n - base;
+        return {&d.ta, d.keys, d.status, base, (int)(rem < per ? rem : per)};
+    }
+};
+
+template <int T, int FPW0, int I, bool LOOKUP, class Src>
+__device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long *ctr) {
+    constexpr int W = kWordsPerBucket / T;
+    constexpr uint32_t TM = (T == 32) ? 0xffffffffu : ((1u << T) - 1u);
+    using E0 = typename std::conditional<(FPW0 >= 2), uint32_t, uint64_t>::type;
+    const int lane = threadIdx.x & 31;
+    const int tl = lane & (T - 1);
+    const int tbase = lane & ~(T - 1);
+    const uint32_t tmask = TM << tbase;
+    const uint32_t last_lane = 1u << (tbase + T - 1);
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t n_probe = 0, n_write = 0, n_ops = 0;
+    int n_fail = 0;
+
+    for (uint64_t c = warp; c < src.nchunks(); c += nwarps) {
+        const WarpChunk ch = src.get(c);
+        const TableArgs &ta = *ch.ta;
+        const Level &L0 = ta.lv[0];
+        const Level &L1 = ta.lv[1];
+        const int FPW1 = L1.fpw;
+        const int LF1 = W * FPW1;
+        const int B1 = kWordsPerBucket * FPW1;
+        const int max_iter = 4 * (kWordsPerBucket * FPW0 + 2 * B1) + 16;
+        const uint64_t *w0 = L0.words + tl * W;
+        const uint64_t *w1 = L1.words + tl * W;
+
+        uint64_t k[I];
+        uint32_t a0[I];
+        E0 e0[I];
+        bool pending[I], lvl2[I];
+        uint8_t st[I];
+        int it[I];
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+            const int pos = i * 32 + lane;
+            const bool has = pos < ch.count;
+            k[i] = has ? load_key(ch.keys, ta.key_bytes, ch.base + pos) : 0;
+            pending[i] = has && valid_key(k[i], ta.w);
+            st[i] = pending[i] ? ST_NOT_FOUND : ST_INVALID;
+            lvl2[i] = false;
+            it[i] = 0;
+            const Quot q = quotient(L0, ta.w, 0, k[i]);
+            a0[i] = (uint32_t)q.a;
+            e0[i] = (E0)(((ta.compact ? q.r : k[i]) << 1) | 1ull);
+        }
+
+        bool any_pending = false;
+#pragma unroll
+        for (int i = 0; i < I; ++i) any_pending |= pending[i];
+        while (__any_sync(0xffffffffu, any_pending)) {
+            // ---- level-1 pass: the primary bucket of every key still at level 1
+            uint32_t pm[I];
+            bool more = false;
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+                pm[i] = __ballot_sync(0xffffffffu, pending[i] && !lvl2[i]) & tmask;
+                more |= pm[i] != 0;
+            }
+            while (__any_sync(0xffffffffu, more)) {
+                int r[I];
+                E0 e[I];
+                uint64_t v[I][W];
+                const uint64_t *p[I];
+#pragma unroll
+                for (int i = 0; i < I; ++i) {
+                    r[i] = pm[i] ? __ffs(pm[i]) - 1 - tbase : -1;
+                    pm[i] &= pm[i] - 1;
+                    const int sl = r[i] & (T - 1);
+                    const uint32_t a = tile_shfl<T>(a0[i], sl);
+                    e[i] = tile_shfl<T>(e0[i], sl);
+                    p[i] = w0 + (uint64_t)a * kWordsPerBucket;
+#pragma unroll
+                    for (int x = 0; x < W; ++x) v[i][x] = 0;
+                    if (r[i] >= 0) load_relaxed<W>(p[i], v[i]);
+                }
+                more = false;
+#pragma unroll
+                for (int i = 0; i < I; ++i) {
+                    more |= pm[i] != 0;
+                    const bool live = r[i] >= 0;
+                    if constexpr (LOOKUP) {
+                        bool m, le;
+                        probe_chunk<W, FPW0>(v[i], e[i], m, le);
+                        const uint32_t bm = __ballot_sync(0xffffffffu, live && m) & tmask;
+                        const uint32_t be = __ballot_sync(0xffffffffu, live && le) & last_lane;
+                        if (tl == r[i]) {
+                            n_probe++;
+                            if (bm) {
+                                st[i] = ST_FOUND;
+                                pending[i] = false;
+                            } else if (be) {
+                                pending[i] = false;  // NOT_FOUND
+                            } else {
+                                lvl2[i] = true;
+                            }
+                        }
+                    } else {
+                        bool m;
+                        int fe;
+                        scan_chunk<W, FPW0>(v[i], e[i], m, fe);
+                        const uint32_t bm = __ballot_sync(0xffffffffu, live && m) & tmask;
+                        const uint32_t be = __ballot_sync(0xffffffffu, live && fe >= 0) & tmask;
+                        const int cl = be ? __ffs(be) - 1 - tbase : 0;
+                        bool claimed = false;
+                        uint64_t seen = 0;
+                        if (live && !bm && be && tl == cl)
+                            claimed = claim_field<FPW0>(const_cast<uint64_t *>(p[i]) + fe / FPW0,
+                                                        fe % FPW0, pick_word<W>(v[i], fe / FPW0),
+                                                        e[i], seen, n_fail);
+                        claimed = tile_shfl<T>(claimed, cl);
+                        seen = tile_shfl<T>(seen, cl);
+                        if (tl == r[i]) {
+                            n_probe++;
+                            if (bm) {
+                                st[i] = ST_FOUND;
+                                pending[i] = false;
+                            } else if (!be) {
+                                lvl2[i] = true;  // level 1 is full for good
+                            } else if (claimed) {
+                                st[i] = ST_PUT;
+                                pending[i] = false;
+                                n_write++;
+                            } else if (seen == (uint64_t)e[i]) {
+                                st[i] = ST_FOUND;  // another thread put k first
+                                pending[i] = false;
+                            } else if (++it[i] > max_iter) {
+                                st[i] = ST_ERROR;
+                                pending[i] = false;
+                                atomicOr(ta.err, 1u);
+                            }
+                        }
+                    }
+                }
+            }
+
+            // ---- level-2 pass: both secondary buckets of every key at level 2
+            uint32_t aa[I], ab[I];
+            uint64_t ea[I], eb[I];
+            more = false;
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+                const bool at2 = pending[i] && lvl2[i];
+                pm[i] = __ballot_sync(0xffffffffu, at2) & tmask;
+                more |= pm[i] != 0;
+                aa[i] = ab[i] = 0;
+                ea[i] = eb[i] = 0;
+                if (at2) {
+                    const Quot qa = quotient(L1, ta.w, 0, k[i]);
+                    const Quot qb = quotient(L1, ta.w, 1, k[i]);
+                    aa[i] = (uint32_t)qa.a;
+                    ab[i] = (uint32_t)qb.a;
+                    ea[i] = ((ta.compact ? qa.r : k[i]) << 2) | 1ull;
+                    eb[i] = ((ta.compact ? qb.r : k[i]) << 2) | 2ull;
+                }
+            }
+            while (__any_sync(0xffffffffu, more)) {
+                more = false;
+#pragma unroll
+                for (int i = 0; i < I; ++i) {
+                    const int r = pm[i] ? __ffs(pm[i]) - 1 - tbase : -1;
+                    pm[i] &= pm[i] - 1;
+                    more |= pm[i] != 0;
+                    const bool live = r >= 0;
+                    const int sl = r & (T - 1);
+                    const uint32_t xa = tile_shfl<T>(aa[i], sl), xb = tile_shfl<T>(ab[i], sl);
+                    const uint64_t ya = tile_shfl<T>(ea[i], sl), yb = tile_shfl<T>(eb[i], sl);
+                    uint64_t *pa = const_cast<uint64_t *>(w1) + (uint64_t)xa * kWordsPerBucket;
+                    uint64_t *pb = const_cast<uint64_t *>(w1) + (uint64_t)xb * kWordsPerBucket;
+                    uint64_t va[W] = {}, vb[W] = {};
+                    if (live) {
+                        load_relaxed<W>(pa, va);
+                        load_relaxed<W>(pb, vb);
+                    }
+                    bool ma, mb;
+                    int fa, fb;
+                    scan_chunk_rt<W>(va, ya, FPW1, ma, fa);
+                    scan_chunk_rt<W>(vb, yb, FPW1, mb, fb);
+                    const uint32_t bfound = __ballot_sync(0xffffffffu, live && (ma || mb)) & tmask;
+                    if constexpr (LOOKUP) {
+                        if (tl == r) {
+                            n_probe += 2;
+                            if (bfound) st[i] = ST_FOUND;
+                            pending[i] = false;
+                        }
+                    } else {
+                        const uint32_t bea = __ballot_sync(0xffffffffu, live && fa >= 0) & tmask;
+                        const uint32_t beb = __ballot_sync(0xffffffffu, live && fb >= 0) & tmask;
+                        const int laa = bea ? __ffs(bea) - 1 - tbase : 0;
+                        const int lab = beb ? __ffs(beb) - 1 - tbase : 0;
+                        const int fea = tile_shfl<T>(fa, laa);
+                        const int feb = tile_shfl<T>(fb, lab);
+                        const int loada = bea ? laa * LF1 + fea : B1;
+                        const int loadb = beb ? lab * LF1 + feb : B1;
+                        // Definition 1: (1, y) precedes (2, y') iff y < y'; ties to the second
+                        const bool pick_a = loada < loadb;
+                        const int load2 = pick_a ? loada : loadb;
+                        const int cl = pick_a ? laa : lab;
+                        bool claimed = false;
+                        uint64_t seen = 0;
+                        if (live && !bfound && load2 < B1 && tl == cl) {
+                            if (pick_a)
+                                claimed = claim_field_rt(FPW1, pa + fa / FPW1, fa % FPW1,
+                                                         pick_word<W>(va, fa / FPW1), ya, seen,
+                                                         n_fail);
+                            else
+                                claimed = claim_field_rt(FPW1, pb + fb / FPW1, fb % FPW1,
+                                                         pick_word<W>(vb, fb / FPW1), yb, seen,
+                                                         n_fail);
+                        }
+                        claimed = tile_shfl<T>(claimed, cl);
+                        seen = tile_shfl<T>(seen, cl);
+                        if (tl == r) {
+                            n_probe += 2;
+                            if (bfound) {
+                                st[i] = ST_FOUND;
+                                pending[i] = false;
+                            } else if (load2 >= B1) {
+                                st[i] = ST_FULL;
+                                pending[i] = false;
+                            } else if (claimed) {
+                                st[i] = ST_PUT;
+                                pending[i] = false;
+                                n_write++;
+                            } else if (seen == (pick_a ? ya : yb)) {
+                                st[i] = ST_FOUND;
+                                pending[i] = false;
+                            } else if (++it[i] > max_iter) {
+                                st[i] = ST_ERROR;
+                                pending[i] = false;
+                                atomicOr(ta.err, 1u);
+                            }
+                        }
+                    }
+                }
+            }
+            any_pending = false;
+#pragma unroll
+            for (int i = 0; i < I; ++i) any_pending |= pending[i];
+        }
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+            const int pos = i * 32 + lane;
+            if (pos < ch.count) ch.status[ch.base + pos] = st[i];
+            n_ops += pos < ch.count ? 1 : 0;
+        }
+    }
+    if (ctr) {
+        flush_counter(ctr, 0, n_probe);
+        flush_counter(ctr, 1, n_write);
+        flush_counter(ctr, 2, (uint64_t)n_fail);
+        flush_counter(ctr, 3, n_ops);
+    }
+}
+
+template <int T, int FPW0, int I, bool LOOKUP>
+__global__ void __launch_bounds__(256)
+    k_iceberg_warp(TableArgs ta, const void *__restrict__ keys, uint64_t n,
+                   uint8_t *__restrict__ status) {
+    SingleSource src{&ta, keys, status, n, (uint64_t)32 * I};
+    iceberg_warp<T, FPW0, I, LOOKUP>(src, ta.ctr);
+}
+
+// one persistent launch over many tables; shared memory holds the prefix of
+// the tables' chunk counts (chunks of 32 * I keys), scanned by the first warp
+template <int T, int FPW0, int I, bool LOOKUP>
+__global__ void __launch_bounds__(256)
+    k_iceberg_batch(const BatchDesc *__restrict__ bd, int count, unsigned long long *ctr) {
+    extern __shared__ uint64_t smem[];
+    uint64_t *prefix = smem;  // count + 1 entries
+    const uint64_t per = (uint64_t)32 * I;
+    if (threadIdx.x < 32) {
+        uint64_t carry = 0;
+        for (int b0 = 0; b0 < count; b0 += 32) {
+            const int t = b0 + (int)threadIdx.x;
+            const uint64_t cnt = t < count ? (bd[t].n + per - 1) / per : 0;
+            uint64_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)threadIdx.x >= o) incl += y;
+            }
+            if (t < count) prefix[t] = carry + incl - cnt;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (threadIdx.x == 0) prefix[count] = carry;
+    }
+    __syncthreads();
+    BatchSource src{bd, prefix, count, per};
+    iceberg_warp<T, FPW0, I, LOOKUP>(src, ctr);
+}
+
+}  // namespace cht
