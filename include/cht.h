@@ -89,7 +89,7 @@ typedef struct cht_table cht_table; /* opaque host handle */
  * tile                  threads cooperating on one bucket: 4, 8 or 16; 0 lets
  *                       each operation use its fastest width (cuckoo puts 4,
  *                       everything else 8).
- * items_per_thread      keys each thread holds per work chunk, 1..8 (0 = 2);
+ * items_per_thread      keys each thread holds per work chunk, 1..8 (0 = 1);
  *                       iceberg operations use 1, 2 or 4 (larger values
  *                       count as 4, 3 as 2).
  * cta_threads           threads per block, a multiple of 32 (0 = 256).
@@ -98,7 +98,7 @@ typedef struct cht_table cht_table; /* opaque host handle */
  *                       With max_tiles = 1 a single tile processes the keys
  *                       strictly in input order (a sequential run).
  * lookups_in_flight     lookups a tile keeps in flight at once in
- *                       cht_find on cuckoo tables: 1, 2 or 4 (0 = 2). More
+ *                       cht_find on cuckoo tables: 1, 2 or 4 (0 = 1). More
  *                       independent bucket loads per tile hide more HBM
  *                       latency at the cost of registers.
  */

@@ -124,7 +124,7 @@ int resolve(const cht_config *in, cht_config *out) {
     // tile 0 stays 0: each operation then uses its own best width
     if (c.tile != 0 && c.tile != 4 && c.tile != 8 && c.tile != 16)
         return fail(CHT_ERR_INVALID, "tile must be 4, 8 or 16 (got %d)", c.tile);
-    if (c.items_per_thread == 0) c.items_per_thread = 2;
+    if (c.items_per_thread == 0) c.items_per_thread = 1;
     if (c.items_per_thread < 1 || c.items_per_thread > 8)
         return fail(CHT_ERR_INVALID, "items_per_thread must be 1..8");
     if (c.cta_threads == 0) c.cta_threads = 256;
@@ -132,7 +132,7 @@ int resolve(const cht_config *in, cht_config *out) {
         return fail(CHT_ERR_INVALID, "cta_threads must be a multiple of 32 in [32, 256]");
     if (c.max_ctas < 0 || c.max_tiles < 0)
         return fail(CHT_ERR_INVALID, "max_ctas and max_tiles must be >= 0");
-    if (c.lookups_in_flight == 0) c.lookups_in_flight = 2;
+    if (c.lookups_in_flight == 0) c.lookups_in_flight = 1;
     if (c.lookups_in_flight != 1 && c.lookups_in_flight != 2 && c.lookups_in_flight != 4)
         return fail(CHT_ERR_INVALID, "lookups_in_flight must be 1, 2 or 4");
     *out = c;
