@@ -136,7 +136,7 @@ def kernel_source_hash() -> str:
 def traffic_per_unit(kernel: str):
     """DRAM bytes per unit of the kernel from the committed ncu summary, if it
     was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    p = os.path.join(ROOT, "profiles", "traffic_per_unit.txt")
     try:
         d = json.load(open(p))[kernel]
     except Exception:
@@ -588,6 +588,46 @@ def run_served(args, dev):
     print(json.dumps(out))
 
 
+def run_profile_case(kind: str, dev):
+    """Small case for ncu captures (a few GB on the device): the 2^24-bucket
+    compact cuckoo table filled to 0.8 (or a 2^22 + 2^19 iceberg table to
+    0.6), then three launches of one kernel over 2^24 keys."""
+    from paper_2406_09255_gb300 import CUCKOO, ICEBERG, Table
+    from paper_2406_09255_gb300 import workloads as W
+    m = 1 << 24
+    st = torch.empty(m, dtype=torch.uint8, device=dev)
+    if kind in ("find", "insert"):
+        seed = W.SEED_BASE + 2
+        t = Table(CUCKOO, 40, 1 << 24, seed=2000, device=dev)
+        n = int(0.8 * t.slots)
+        pre = n if kind == "find" else n - 3 * m
+        keys = W.unique_keys(0, pre, 40, seed, device=dev)
+        t.insert(keys)
+        del keys
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        if kind == "find":
+            q, _ = W.find_queries(n, m, 0.5, 40, seed, n, device=dev)
+            for _ in range(3):
+                t.find(q, status=st)
+        else:
+            for i in range(3):
+                t.insert(W.unique_keys(pre + i * m, m, 40, seed, device=dev), status=st)
+    else:
+        seed = W.SEED_BASE + 3
+        t = Table(ICEBERG, 48, 1 << 22, 1 << 19, seed=3000, device=dev)
+        n = int(0.6 * t.slots)
+        t.find_or_put(W.unique_keys(0, n - 3 * m, 48, seed, device=dev))
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        for i in range(3):
+            k = W.unique_keys(n - 3 * m + i * m // 2, m, 48, seed, device=dev)  # half repeats
+            t.find_or_put(k, status=st)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": kind, "ok": True,
+                      "max_gib": torch.cuda.max_memory_allocated(dev) / 2 ** 30}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -600,7 +640,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=4000, help="served workload: request count")
+    ap.add_argument("--profile", choices=["find", "insert", "fop"],
+                    help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
+    if args.profile:
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        import __graft_entry__
+        __graft_entry__.build()
+        run_profile_case(args.profile, dev)
+        return 0
     if args.workload in others:
         assert args.warmup >= 1
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
