@@ -235,21 +235,30 @@ struct Swar {
 };
 
 // per-lane scan of the owned fields: whether one equals `entry`, and the local
-// index of the first EMPTY field (-1 if none)
+// index at which to claim: W * FPW minus the number of EMPTY fields, or -1 if
+// none is empty.
+//
+// Filled slots of a bucket form a prefix, so in a consistent snapshot this is
+// the first empty field (and the zero-field mask is then exact, one flag per
+// empty field). A snapshot torn across words may show stale empties; since a
+// field never becomes empty again, the snapshot's empty fields include every
+// field that is truly empty, so the index is never past the true first empty
+// slot: a claim there either hits exactly the first empty slot or finds its
+// field taken and fails, as any lost race does.
 template <int W, int FPW>
 __device__ __forceinline__ void scan_chunk(const uint64_t (&v)[W], uint64_t entry, bool &match,
                                            int &first_empty) {
     using Z = Swar<FPW>;
     const uint64_t pat = Z::spread(entry);
     uint64_t hit = 0;
-    first_empty = -1;
+    int empties = 0;
 #pragma unroll
-    for (int i = W - 1; i >= 0; --i) {
+    for (int i = 0; i < W; ++i) {
         hit |= Z::zeros(v[i] ^ pat);
-        const uint64_t z = Z::zeros(v[i]);
-        if (z) first_empty = i * FPW + (__ffsll((long long)z) - 1) / Z::S;
+        empties += __popcll(Z::zeros(v[i]));
     }
     match = hit != 0;
+    first_empty = empties ? W * FPW - empties : -1;
 }
 
 // lookup form of the scan: whether some owned field equals `entry`, and

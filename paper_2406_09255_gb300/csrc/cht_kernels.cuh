@@ -155,13 +155,15 @@ __global__ void __launch_bounds__(256)
 // Work sharing as in Algorithm 3, with the per-key arithmetic taken out of
 // the tile: every lane loads one key of the warp's 32 and computes its own
 // bucket address and entry; then each tile of T lanes walks the keys of its
-// own lanes, U at a time. It broadcasts their addresses (Shuffle), loads the
-// U buckets back to back (for T = 8 one 16-byte read per lane and bucket, so
-// one warp load instruction fetches four whole lines) and answers each key
-// with two ballots (Any match, Any empty). A key whose bucket was full and
-// did not hold it moves to hash j + 1 in the next pass. The table is not
-// written while a lookup runs (static table), so buckets are read through
-// the non-coherent path without L1 allocation.
+// own lanes, one per round. It broadcasts the key's bucket index and entry
+// (Shuffle), loads the bucket (for T = 8 one 16-byte read per lane, so one
+// warp load instruction fetches four whole lines) and answers with two
+// ballots (Any match, last slot empty). A key whose bucket was full and did
+// not hold it moves to hash j + 1 in the next pass. With U = 2 the bucket of
+// the next round is loaded before the current one is inspected, so a load is
+// always in flight. The table is not written while a lookup runs (static
+// table), so buckets are read through the non-coherent path without L1
+// allocation.
 // ===========================================================================
 template <int T, int FPW, int U>
 __global__ void __launch_bounds__(256, U == 1 ? 6 : (U == 2 ? 5 : 4))
@@ -180,11 +182,9 @@ __global__ void __launch_bounds__(256, U == 1 ? 6 : (U == 2 ? 5 : 4))
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) << 5;
     uint64_t n_probe = 0, n_ops = 0;
-    uint64_t v[U][W];
+    uint64_t va[W], vb[W];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int i = 0; i < W; ++i) v[u][i] = 0;
+    for (int i = 0; i < W; ++i) va[i] = vb[i] = 0;
 
     uint64_t base = warp * 32;
     uint64_t k_next = (base + lane < n) ? load_key(keys, ta.key_bytes, base + lane) : 0;
@@ -207,40 +207,52 @@ __global__ void __launch_bounds__(256, U == 1 ? 6 : (U == 2 ? 5 : 4))
                 entry = (Entry)((((ta.compact ? qt.r : k)) << 2) | (uint64_t)(j + 1));
             }
             // this pass: every key of the tile still pending, at its own hash j
-            uint32_t pm = tile_ballot<T>(pending);
-            while (__any_sync(0xffffffffu, pm != 0)) {
-                int r[U];
-                Entry e[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    r[u] = pm ? __ffs(pm) - 1 : -1;
+            uint32_t pm = __ballot_sync(0xffffffffu, pending) & tmask;
+            // round "a" is loaded; with U = 2 round "b" is loaded ahead of it
+            int ra = pm ? __ffs(pm) - 1 - tbase : -1;
+            pm &= pm - 1;
+            Entry ea = tile_shfl<T>(entry, ra & (T - 1));
+            {
+                const uint32_t a = tile_shfl<T>(addr, ra & (T - 1));
+                load_stream_if<W>(ra >= 0, words + (uint64_t)a * kWordsPerBucket, va);
+            }
+            while (__any_sync(0xffffffffu, ra >= 0)) {
+                int rb = -1;
+                Entry eb = 0;
+                if constexpr (U >= 2) {
+                    rb = pm ? __ffs(pm) - 1 - tbase : -1;
                     pm &= pm - 1;
+                    eb = tile_shfl<T>(entry, rb & (T - 1));
+                    const uint32_t a = tile_shfl<T>(addr, rb & (T - 1));
+                    load_stream_if<W>(rb >= 0, words + (uint64_t)a * kWordsPerBucket, vb);
                 }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int src = r[u] & (T - 1);
-                    const uint32_t a = tile_shfl<T>(addr, src);
-                    e[u] = tile_shfl<T>(entry, src);
-                    load_stream_if<W>(r[u] >= 0, words + (uint64_t)a * kWordsPerBucket, v[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    bool m, le;
-                    probe_chunk<W, FPW>(v[u], e[u], m, le);
-                    const bool live = r[u] >= 0;
-                    const uint32_t bm = __ballot_sync(0xffffffffu, live && m) & tmask;
-                    const uint32_t be = __ballot_sync(0xffffffffu, live && le) & last_lane;
-                    if (tl == r[u]) {
-                        n_probe++;
-                        if (bm) {
-                            st = ST_FOUND;
-                            pending = false;
-                        } else if (be || j + 1 >= ta.H) {
-                            pending = false;
-                        } else {
-                            j++;
-                        }
+                bool m, le;
+                probe_chunk<W, FPW>(va, ea, m, le);
+                const bool live = ra >= 0;
+                const uint32_t bm = __ballot_sync(0xffffffffu, live && m) & tmask;
+                const uint32_t be = __ballot_sync(0xffffffffu, live && le) & last_lane;
+                if (tl == ra) {
+                    n_probe++;
+                    if (bm) {
+                        st = ST_FOUND;
+                        pending = false;
+                    } else if (be || j + 1 >= ta.H) {
+                        pending = false;
+                    } else {
+                        j++;  // probe a_{j+1} in the next pass
                     }
+                }
+                if constexpr (U >= 2) {
+                    ra = rb;
+                    ea = eb;
+#pragma unroll
+                    for (int i = 0; i < W; ++i) va[i] = vb[i];
+                } else {
+                    ra = pm ? __ffs(pm) - 1 - tbase : -1;
+                    pm &= pm - 1;
+                    ea = tile_shfl<T>(entry, ra & (T - 1));
+                    const uint32_t a = tile_shfl<T>(addr, ra & (T - 1));
+                    load_stream_if<W>(ra >= 0, words + (uint64_t)a * kWordsPerBucket, va);
                 }
             }
         }

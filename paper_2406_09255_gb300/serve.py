@@ -208,6 +208,16 @@ class Server:
             for group, op in ((finds, OP_FIND), (fops, OP_FIND_OR_PUT)):
                 if not group:
                     continue
+                if len(group) == 1:
+                    # a lone request needs no fused plan: one direct launch
+                    r = group[0]
+                    t = self.states[r.table].table
+                    if op == OP_FIND:
+                        t.find(r.keys, status=r.status, stream=s)
+                    else:
+                        t.find_or_put(r.keys, status=r.status, stream=s)
+                    self.launches += 1
+                    continue
                 # one fused launch; several lookups of one table are
                 # concatenated into one entry (lookups commute)
                 by_table: dict[int, list[Request]] = {}
