@@ -577,7 +577,7 @@ def run_served(args, dev):
     srv.plan(reqs, seed=1)
     run_sequential(srv, reqs, realtime=False)
     results["saturated_sync"] = latency_stats(reqs)
-    for frac in (0.25, 0.5, 0.9, 1.2):
+    for frac in (0.25, 0.5, 0.9, 1.2, 1.5, 2.0):
         rate = frac * sat_rate
         row = {}
         for mode in ("served", "sync_per_request"):

@@ -3,6 +3,7 @@
 // of the hot-path kernels. No device memory is allocated here.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -507,8 +508,16 @@ int cht_batch_create(cht_table *const *tables, const void *const *d_keys, const 
         b->host[i].n = n[i];
         b->host[i].status = d_status[i];
     }
-    cudaError_t ce = cudaMemcpyAsync(b->dev, b->host.data(), sizeof(BatchDesc) * count,
-                                     cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+    // descriptors travel as kernel parameters (kDescPerLaunch per launch): the
+    // upload is asynchronous and leaves no host buffer to keep alive
+    cudaError_t ce = cudaSuccess;
+    for (int i0 = 0; i0 < count && ce == cudaSuccess; i0 += kDescPerLaunch) {
+        const int m = std::min(kDescPerLaunch, count - i0);
+        DescBlock blk;
+        memcpy(blk.d, b->host.data() + i0, sizeof(BatchDesc) * m);
+        k_write_desc<<<1, 128, 0, static_cast<cudaStream_t>(stream)>>>(b->dev + i0, blk, m);
+        ce = cudaGetLastError();
+    }
     if (ce != cudaSuccess) {
         delete b;
         return cuda_fail(ce, "uploading batch descriptors");

@@ -92,6 +92,20 @@ __global__ void __launch_bounds__(256) k_clear_batch(const BatchDesc *__restrict
     }
 }
 
+// batch descriptors carried to the device as kernel parameters: the upload is
+// then an ordinary asynchronous launch, with no host buffer to keep alive
+constexpr int kDescPerLaunch = 64;
+struct DescBlock {
+    BatchDesc d[kDescPerLaunch];
+};
+__global__ void __launch_bounds__(128) k_write_desc(BatchDesc *__restrict__ dst, DescBlock blk,
+                                                    int count) {
+    const uint64_t *src = reinterpret_cast<const uint64_t *>(blk.d);
+    uint64_t *out = reinterpret_cast<uint64_t *>(dst);
+    const int words = count * (int)(sizeof(BatchDesc) / 8);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) out[i] = src[i];
+}
+
 // zero n16 16-byte units starting at p (16-byte aligned)
 __global__ void __launch_bounds__(256) k_clear(ulonglong2 *p, uint64_t n16) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
