@@ -747,7 +747,7 @@ def main():
     tpu = traffic_per_unit("cuckoo_find")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": (tpu * wl.nq) if tpu else None,
-                "kernel": "k_cuckoo_find<8,3>", "peak_source": f"{peak_kind} hbm_gbs",
+                "kernel": "k_cuckoo_find_stream<8,3,4>", "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": fb / (fq / wl.nq)}
 
     e2e = None

@@ -97,10 +97,14 @@ typedef struct cht_table cht_table; /* opaque host handle */
  * max_tiles             upper bound on tiles that take work (0 = no bound).
  *                       With max_tiles = 1 a single tile processes the keys
  *                       strictly in input order (a sequential run).
- * lookups_in_flight     lookups a tile keeps in flight at once in
- *                       cht_find on cuckoo tables: 1, 2 or 4 (0 = 1). More
- *                       independent bucket loads per tile hide more HBM
- *                       latency at the cost of registers.
+ * lookups_in_flight     bucket loads a tile keeps in flight in cht_find on
+ *                       cuckoo tables: 1, 4 or 8 (0 = 4). With 1 each tile
+ *                       walks its pending keys one load at a time; with 4 or
+ *                       8 every lane holds a key, each round probes all of a
+ *                       tile's keys with that many loads issued back to back,
+ *                       and answered lanes take the next key (a stream of
+ *                       fully packed rounds). Answers and probe counts are
+ *                       the same for every value.
  */
 typedef struct cht_config {
     int32_t kind;

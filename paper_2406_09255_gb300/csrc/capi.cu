@@ -133,9 +133,9 @@ int resolve(const cht_config *in, cht_config *out) {
         return fail(CHT_ERR_INVALID, "cta_threads must be a multiple of 32 in [32, 256]");
     if (c.max_ctas < 0 || c.max_tiles < 0)
         return fail(CHT_ERR_INVALID, "max_ctas and max_tiles must be >= 0");
-    if (c.lookups_in_flight == 0) c.lookups_in_flight = 1;
-    if (c.lookups_in_flight != 1 && c.lookups_in_flight != 2 && c.lookups_in_flight != 4)
-        return fail(CHT_ERR_INVALID, "lookups_in_flight must be 1, 2 or 4");
+    if (c.lookups_in_flight == 0) c.lookups_in_flight = 4;
+    if (c.lookups_in_flight != 1 && c.lookups_in_flight != 4 && c.lookups_in_flight != 8)
+        return fail(CHT_ERR_INVALID, "lookups_in_flight must be 1, 4 or 8");
     *out = c;
     return CHT_OK;
 }

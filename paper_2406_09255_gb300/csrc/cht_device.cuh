@@ -188,6 +188,54 @@ __device__ __forceinline__ void load_stream_if(bool p, const uint64_t *ptr, uint
     }
 }
 
+// load_relaxed under a predicate, for callers that ignore v when p is false
+// (v is then left unspecified)
+template <int W>
+__device__ __forceinline__ void load_relaxed_or_skip(bool p, const uint64_t *ptr,
+                                                     uint64_t (&v)[W]) {
+    const unsigned pr = p ? 1u : 0u;
+    if constexpr (W == 1) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+            "@q ld.relaxed.gpu.global.u64 %0, [%1];\n\t}"
+            : "=l"(v[0])
+            : "l"(ptr), "r"(pr)
+            : "memory");
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2)
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t"
+                "@q ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];\n\t}"
+                : "=l"(v[i]), "=l"(v[i + 1])
+                : "l"(ptr + i), "r"(pr)
+                : "memory");
+    }
+}
+
+// load_stream under a predicate, for callers that ignore v when p is false:
+// v is then left unspecified, which saves initialising it
+template <int W>
+__device__ __forceinline__ void load_stream_or_skip(bool p, const uint64_t *ptr,
+                                                    uint64_t (&v)[W]) {
+    const unsigned pr = p ? 1u : 0u;
+    if constexpr (W == 1) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+            "@q ld.global.nc.L1::no_allocate.u64 %0, [%1];\n\t}"
+            : "=l"(v[0])
+            : "l"(ptr), "r"(pr));
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2)
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t"
+                "@q ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];\n\t}"
+                : "=l"(v[i]), "=l"(v[i + 1])
+                : "l"(ptr + i), "r"(pr));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Tile primitives. A tile is T consecutive lanes of a warp; every lane of the
 // warp executes these together (full-warp masks), each tile reading its own
@@ -369,6 +417,82 @@ __device__ __forceinline__ uint64_t swap_field(uint64_t *wp, int f, uint64_t sna
         }
         ok = false;
         return 0;
+    }
+}
+
+// The same two operations split in two phases, so that a thread can have the
+// atomics of several buckets in flight: field_op_issue makes the first
+// attempt (a claim when `swap` is false, else a swap) and returns the value
+// the atomic saw together with the value it expected; field_op_finish reads
+// the outcome and, in the rare case where only a neighbouring field of a
+// packed word changed, continues with the retry loops above.
+template <int FPW>
+__device__ __forceinline__ uint64_t field_op_issue(bool swap, uint64_t *wp, int f, uint64_t snap_word,
+                                                   uint64_t entry, uint64_t &expected) {
+    using F = Fields<FPW>;
+    if constexpr (FPW == 1) {
+        expected = 0ull;
+        if (swap) {
+            const uint64_t old = atomicExch(reinterpret_cast<unsigned long long *>(wp),
+                                            static_cast<unsigned long long>(entry));
+            expected = old;
+            return old;
+        }
+        return atomicCAS(reinterpret_cast<unsigned long long *>(wp), 0ull,
+                         static_cast<unsigned long long>(entry));
+    } else if constexpr (FPW == 2) {
+        unsigned int *hp = reinterpret_cast<unsigned int *>(wp) + f;
+        if (swap) {
+            const uint64_t old = atomicExch(hp, static_cast<unsigned int>(entry));
+            expected = old;
+            return old;
+        }
+        expected = 0;
+        return atomicCAS(hp, 0u, static_cast<unsigned int>(entry));
+    } else {
+        if (FPW == 4 && !swap) {
+            unsigned short *hp = reinterpret_cast<unsigned short *>(wp) + f;
+            expected = 0;
+            return atomicCAS(hp, static_cast<unsigned short>(0), static_cast<unsigned short>(entry));
+        }
+        expected = snap_word & ~(F::M << (f * F::S));
+        if (swap) expected = snap_word;
+        const uint64_t desired = (snap_word & ~(F::M << (f * F::S))) | (entry << (f * F::S));
+        return atomicCAS(reinterpret_cast<unsigned long long *>(wp), expected, desired);
+    }
+}
+
+// outcome of a claim: true if written, else seen = the field value that won
+template <int FPW>
+__device__ __forceinline__ bool claim_finish(uint64_t *wp, int f, uint64_t old, uint64_t expected,
+                                             uint64_t entry, uint64_t &seen, int &fails) {
+    using F = Fields<FPW>;
+    if (old == expected) return true;
+    fails++;
+    if constexpr (FPW == 1 || FPW == 2 || FPW == 4) {
+        seen = old;  // a whole-field CAS: the winner's value
+        return false;
+    } else {
+        const uint64_t fld = F::get(old, f);
+        if (fld != 0) {
+            seen = fld;
+            return false;
+        }
+        return claim_field<FPW>(wp, f, old, entry, seen, fails);  // a neighbour changed
+    }
+}
+
+// outcome of a swap: the previous field value; ok = false if the retry gave up
+template <int FPW>
+__device__ __forceinline__ uint64_t swap_finish(uint64_t *wp, int f, uint64_t old,
+                                                uint64_t expected, uint64_t entry, bool &ok) {
+    using F = Fields<FPW>;
+    ok = true;
+    if constexpr (FPW == 1 || FPW == 2) {
+        return old;  // a native exchange always succeeds
+    } else {
+        if (old == expected) return F::get(old, f);
+        return swap_field<FPW>(wp, f, old, entry, ok);
     }
 }
 

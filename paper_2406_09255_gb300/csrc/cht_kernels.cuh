@@ -159,14 +159,15 @@ __global__ void __launch_bounds__(256)
 // (Shuffle), loads the bucket (for T = 8 one 16-byte read per lane, so one
 // warp load instruction fetches four whole lines) and answers with two
 // ballots (Any match, last slot empty). A key whose bucket was full and did
-// not hold it moves to hash j + 1 in the next pass. With U = 2 the bucket of
-// the next round is loaded before the current one is inspected, so a load is
-// always in flight. The table is not written while a lookup runs (static
-// table), so buckets are read through the non-coherent path without L1
-// allocation.
+// not hold it moves to hash j + 1 in the next pass. The table is not written
+// while a lookup runs (static table), so buckets are read through the
+// non-coherent path without L1 allocation.
+//
+// This form keeps one bucket load in flight per tile; the stream form below
+// is the fast path and this one its plain counterpart.
 // ===========================================================================
-template <int T, int FPW, int U>
-__global__ void __launch_bounds__(256, U == 1 ? 6 : (U == 2 ? 5 : 4))
+template <int T, int FPW>
+__global__ void __launch_bounds__(256, 6)
     k_cuckoo_find(TableArgs ta, const void *__restrict__ keys, uint64_t n,
                   uint8_t *__restrict__ status) {
     constexpr int W = kWordsPerBucket / T;
@@ -182,9 +183,9 @@ __global__ void __launch_bounds__(256, U == 1 ? 6 : (U == 2 ? 5 : 4))
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) << 5;
     uint64_t n_probe = 0, n_ops = 0;
-    uint64_t va[W], vb[W];
+    uint64_t v[W];
 #pragma unroll
-    for (int i = 0; i < W; ++i) va[i] = vb[i] = 0;
+    for (int i = 0; i < W; ++i) v[i] = 0;
 
     uint64_t base = warp * 32;
     uint64_t k_next = (base + lane < n) ? load_key(keys, ta.key_bytes, base + lane) : 0;
@@ -208,30 +209,20 @@ __global__ void __launch_bounds__(256, U == 1 ? 6 : (U == 2 ? 5 : 4))
             }
             // this pass: every key of the tile still pending, at its own hash j
             uint32_t pm = __ballot_sync(0xffffffffu, pending) & tmask;
-            // round "a" is loaded; with U = 2 round "b" is loaded ahead of it
-            int ra = pm ? __ffs(pm) - 1 - tbase : -1;
+            int r = pm ? __ffs(pm) - 1 - tbase : -1;
             pm &= pm - 1;
-            Entry ea = tile_shfl<T>(entry, ra & (T - 1));
+            Entry e = tile_shfl<T>(entry, r & (T - 1));
             {
-                const uint32_t a = tile_shfl<T>(addr, ra & (T - 1));
-                load_stream_if<W>(ra >= 0, words + (uint64_t)a * kWordsPerBucket, va);
+                const uint32_t a = tile_shfl<T>(addr, r & (T - 1));
+                load_stream_if<W>(r >= 0, words + (uint64_t)a * kWordsPerBucket, v);
             }
-            while (__any_sync(0xffffffffu, ra >= 0)) {
-                int rb = -1;
-                Entry eb = 0;
-                if constexpr (U >= 2) {
-                    rb = pm ? __ffs(pm) - 1 - tbase : -1;
-                    pm &= pm - 1;
-                    eb = tile_shfl<T>(entry, rb & (T - 1));
-                    const uint32_t a = tile_shfl<T>(addr, rb & (T - 1));
-                    load_stream_if<W>(rb >= 0, words + (uint64_t)a * kWordsPerBucket, vb);
-                }
+            while (__any_sync(0xffffffffu, r >= 0)) {
                 bool m, le;
-                probe_chunk<W, FPW>(va, ea, m, le);
-                const bool live = ra >= 0;
+                probe_chunk<W, FPW>(v, e, m, le);
+                const bool live = r >= 0;
                 const uint32_t bm = __ballot_sync(0xffffffffu, live && m) & tmask;
                 const uint32_t be = __ballot_sync(0xffffffffu, live && le) & last_lane;
-                if (tl == ra) {
+                if (tl == r) {
                     n_probe++;
                     if (bm) {
                         st = ST_FOUND;
@@ -242,22 +233,138 @@ __global__ void __launch_bounds__(256, U == 1 ? 6 : (U == 2 ? 5 : 4))
                         j++;  // probe a_{j+1} in the next pass
                     }
                 }
-                if constexpr (U >= 2) {
-                    ra = rb;
-                    ea = eb;
-#pragma unroll
-                    for (int i = 0; i < W; ++i) va[i] = vb[i];
-                } else {
-                    ra = pm ? __ffs(pm) - 1 - tbase : -1;
-                    pm &= pm - 1;
-                    ea = tile_shfl<T>(entry, ra & (T - 1));
-                    const uint32_t a = tile_shfl<T>(addr, ra & (T - 1));
-                    load_stream_if<W>(ra >= 0, words + (uint64_t)a * kWordsPerBucket, va);
-                }
+                r = pm ? __ffs(pm) - 1 - tbase : -1;
+                pm &= pm - 1;
+                e = tile_shfl<T>(entry, r & (T - 1));
+                const uint32_t a = tile_shfl<T>(addr, r & (T - 1));
+                load_stream_if<W>(r >= 0, words + (uint64_t)a * kWordsPerBucket, v);
             }
         }
         if (has) status[idx] = st;
         n_ops += has ? 1 : 0;
+    }
+    if (ta.ctr) {
+        flush_counter(ta.ctr, 0, n_probe);
+        flush_counter(ta.ctr, 3, n_ops);
+    }
+}
+
+// ===========================================================================
+// The lookup of Section 4.4 as a stream of probe rounds (the fast path).
+// Each lane holds one key at a time with its current hash index j. In every
+// round each tile probes all of its lanes' keys on a fixed schedule: tile
+// lane s's key goes in slot s, and Q bucket loads are issued back to back
+// before any is inspected (Q lines in flight per tile), with no search for
+// pending keys. Match flags are gathered per lane as bit s of a mask and
+// OR-reduced over the tile once per round; the last lane's "last slot empty"
+// flags come back in one broadcast. A lane whose key is answered writes the
+// status and takes the next key of the warp's stream (the warp's grid-stride
+// 32-key chunks in order) for the next round, so every round is fully packed
+// whatever mix of j the keys are at: the waiting lanes are ranked with one
+// ballot and served from two chunks of keys held one per lane and read ahead
+// of use. Probes per key, and so the answers and probe counts, are those of
+// the per-round form.
+// ===========================================================================
+template <int T, int FPW, int Q>
+__global__ void __launch_bounds__(256, 3)
+    k_cuckoo_find_stream(TableArgs ta, const void *__restrict__ keys, uint64_t n,
+                         uint8_t *__restrict__ status) {
+    constexpr int W = kWordsPerBucket / T;
+    constexpr int QE = Q < T ? Q : T;
+    static_assert(T % QE == 0, "slots split evenly into load groups");
+    using Entry = typename std::conditional<(FPW >= 2), uint32_t, uint64_t>::type;
+    const int lane = threadIdx.x & 31;
+    const int tl = lane & (T - 1);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const Level &L = ta.lv[0];
+    const uint64_t *words = L.words + tl * W;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) << 5;
+    uint64_t n_probe = 0, n_ops = 0;
+
+    // key buffers: chunk A at baseA (next key at offset o), chunk B at baseA + stride
+    uint64_t baseA = warp * 32;
+    uint64_t kA = (baseA + lane < n) ? load_key(keys, ta.key_bytes, baseA + lane) : 0;
+    uint64_t kB = (baseA + stride + lane < n) ? load_key(keys, ta.key_bytes, baseA + stride + lane)
+                                              : 0;
+    int o = 0;
+    uint64_t k = 0, idx = 0;
+    int j = 0;
+    bool live = false;
+    while (true) {
+        // refill the lanes without a key, in rank order
+        const uint32_t need = __ballot_sync(0xffffffffu, !live);
+        if (need) {
+            const int src = o + __popc(need & lt_mask);
+            const uint64_t ka = __shfl_sync(0xffffffffu, kA, src & 31);
+            const uint64_t kb = __shfl_sync(0xffffffffu, kB, src & 31);
+            if (!live) {
+                idx = src < 32 ? baseA + src : baseA + stride + (src - 32);
+                if (idx < n) {
+                    k = src < 32 ? ka : kb;
+                    j = 0;
+                    n_ops++;
+                    if (valid_key(k, ta.w))
+                        live = true;
+                    else
+                        status[idx] = ST_INVALID;
+                }
+            }
+            o += __popc(need);
+            if (o >= 32) {
+                o -= 32;
+                baseA += stride;
+                kA = kB;
+                const uint64_t nb = baseA + stride + lane;
+                kB = nb < n ? load_key(keys, ta.key_bytes, nb) : 0;
+            }
+        }
+        if (!__any_sync(0xffffffffu, live)) {
+            if (baseA >= n) break;  // the warp's stream is exhausted
+            continue;               // a round of invalid keys only
+        }
+        uint32_t addr = 0;
+        Entry entry = 0;
+        if (live) {
+            const Quot qt = quotient(L, ta.w, j, k);
+            addr = (uint32_t)qt.a;
+            entry = (Entry)(((ta.compact ? qt.r : k) << 2) | (uint64_t)(j + 1));
+        }
+        const uint32_t pb = tile_ballot<T>(live);
+        uint32_t mbits = 0, lbits = 0;
+#pragma unroll
+        for (int s0 = 0; s0 < T; s0 += QE) {
+            uint64_t v[QE][W];
+#pragma unroll
+            for (int q = 0; q < QE; ++q) {
+                const uint32_t a = tile_shfl<T>(addr, s0 + q);
+                load_stream_or_skip<W>((pb >> (s0 + q)) & 1u,
+                                       words + (uint64_t)a * kWordsPerBucket, v[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < QE; ++q) {
+                const Entry e = tile_shfl<T>(entry, s0 + q);
+                bool m, le;
+                probe_chunk<W, FPW>(v[q], e, m, le);
+                mbits |= (m ? 1u : 0u) << (s0 + q);
+                lbits |= (le ? 1u : 0u) << (s0 + q);
+            }
+        }
+#pragma unroll
+        for (int off = 1; off < T; off <<= 1) mbits |= __shfl_xor_sync(0xffffffffu, mbits, off);
+        lbits = tile_shfl<T>(lbits, T - 1);
+        if (live) {
+            n_probe++;
+            if ((mbits >> tl) & 1u) {
+                status[idx] = ST_FOUND;
+                live = false;
+            } else if (((lbits >> tl) & 1u) || j + 1 >= ta.H) {
+                status[idx] = ST_NOT_FOUND;
+                live = false;
+            } else {
+                j++;
+            }
+        }
     }
     if (ta.ctr) {
         flush_counter(ta.ctr, 0, n_probe);

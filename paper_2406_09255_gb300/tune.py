@@ -113,36 +113,46 @@ def tune_batch(batch, reps: int = 3, use_cache: bool = True, tiles=TILES, items=
 
 
 def tune_table(table, op: str, keys: torch.Tensor, reps: int = 3, use_cache: bool = True,
-               tiles=TILES, items=ITEMS) -> dict:
-    """Pick (tile, items_per_thread) for one operation on one table
-    ("find", "insert" or "find_or_put"); applies and returns it."""
+               tiles=TILES, items=ITEMS, in_flight=None) -> dict:
+    """Pick the launch shape for one operation on one table ("find", "insert"
+    or "find_or_put"); applies and returns it. Candidates are (tile,
+    items_per_thread) pairs with the table's lookups_in_flight and, on cuckoo
+    tables, also each tile with 4 or 8 loads in flight (the stream kernels,
+    which take no items_per_thread)."""
     key = shape_key(op, [table])
     if use_cache:
         hit = _load_cache().get(key)
         if hit:
             table.set_launch(tile=hit["tile"], items_per_thread=hit["items"],
-                             lookups_in_flight=table.cfg.lookups_in_flight)
+                             lookups_in_flight=hit.get("in_flight",
+                                                       table.cfg.lookups_in_flight))
             return dict(hit, cached=True)
+    if in_flight is None:
+        in_flight = (1, 4, 8) if (table.cfg.kind == 0 and op != "find_or_put") else (
+            table.cfg.lookups_in_flight,)
+    cands = []
+    for P in in_flight:
+        for T in tiles:
+            for I in (items if P == 1 else (1,)):
+                cands.append((T, I, P))
     snap = table.storage.clone()
     status = torch.empty(keys.numel(), dtype=torch.uint8, device=keys.device)
     fn = getattr(table, op)
     results = []
-    for T in tiles:
-        for I in items:
-            table.set_launch(tile=T, items_per_thread=I,
-                             lookups_in_flight=table.cfg.lookups_in_flight)
-            ms = []
-            for _ in range(reps):
-                table.storage.copy_(snap)
-                torch.cuda.synchronize()
-                ms.append(_time(lambda: fn(keys, status=status), 1))
-            results.append((statistics.median(ms), T, I))
+    for T, I, P in cands:
+        table.set_launch(tile=T, items_per_thread=I, lookups_in_flight=P)
+        ms = []
+        for _ in range(reps):
+            table.storage.copy_(snap)
+            torch.cuda.synchronize()
+            ms.append(_time(lambda: fn(keys, status=status), 1))
+        results.append((statistics.median(ms), T, I, P))
     table.storage.copy_(snap)
     torch.cuda.synchronize()
     best = min(results)
-    table.set_launch(tile=best[1], items_per_thread=best[2],
-                     lookups_in_flight=table.cfg.lookups_in_flight)
-    out = {"tile": best[1], "items": best[2], "ms": best[0]}
+    table.set_launch(tile=best[1], items_per_thread=best[2], lookups_in_flight=best[3])
+    out = {"tile": best[1], "items": best[2], "in_flight": best[3], "ms": best[0]}
     if use_cache:
         _store(key, out)
-    return dict(out, cached=False, sweep=[{"tile": T, "items": I, "ms": m} for m, T, I in results])
+    return dict(out, cached=False,
+                sweep=[{"tile": T, "items": I, "in_flight": P, "ms": m} for m, T, I, P in results])

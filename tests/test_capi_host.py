@@ -53,6 +53,7 @@ def test_workload_layouts(lib):
     # -> three fields per word, 48 slots per bucket, 786,432 slots
     code, c = _resolve(lib, kind=0, key_bits=32, key_bytes=4, num_buckets=1 << 14)
     assert code == 0 and c.fields_per_word == 3 and c.num_hashes == 3
+    assert c.lookups_in_flight == 4  # default: the stream form, four loads per tile
     assert (1 << 14) * 16 * c.fields_per_word == 786432
     # 2^24 buckets, 40-bit keys: 16 + 2 bits -> three per word (805,306,368 slots), 2 GiB
     code, c = _resolve(lib, kind=0, key_bits=40, num_buckets=1 << 24)
@@ -95,6 +96,8 @@ def test_bit_budget_section_5_1(lib):
     (dict(kind=0, key_bits=32, num_buckets=16, cta_threads=48), "cta_threads"),
     (dict(kind=1, key_bits=32, num_buckets=16, num_buckets_backyard=0), "backyard"),
     (dict(kind=0, key_bits=62, num_buckets=4, fields_per_word=2), "bits"),
+    (dict(kind=0, key_bits=32, num_buckets=16, lookups_in_flight=2), "lookups_in_flight"),
+    (dict(kind=0, key_bits=32, num_buckets=16, lookups_in_flight=16), "lookups_in_flight"),
 ])
 def test_invalid_configs_rejected_with_message(lib, kw, frag):
     code, _ = _resolve(lib, **kw)

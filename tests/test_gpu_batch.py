@@ -160,3 +160,26 @@ def test_tuner_picks_a_valid_shape(tmp_path, monkeypatch):
         check_table(t, k, s)
     r2 = tune_batch(b, reps=1)
     assert r2["cached"] and r2["tile"] == r["tile"]
+
+
+def test_table_tuner_sweeps_loads_in_flight(tmp_path, monkeypatch):
+    """tune_table on a cuckoo table tries the chunk put (one load in flight,
+    several items per lane) and the stream put (4 or 8 loads in flight),
+    restores the table after every trial and applies the winner, which then
+    stores every key."""
+    monkeypatch.setenv("CHT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    from paper_2406_09255_gb300.tune import tune_table
+    t = P().Table(P().CUCKOO, 32, 1 << 12, key_bytes=4, seed=44)
+    n = int(0.85 * t.slots)
+    keys = W.to_u32(W.unique_keys(0, n, 32, 4040)).to(DEV)
+    r = tune_table(t, "insert", keys, reps=1, tiles=(4, 8), items=(1, 2))
+    shapes = {(x["tile"], x["items"], x["in_flight"]) for x in r["sweep"]}
+    assert shapes == {(4, 1, 1), (4, 2, 1), (8, 1, 1), (8, 2, 1),
+                      (4, 1, 4), (8, 1, 4), (4, 1, 8), (8, 1, 8)}
+    assert (r["tile"], r["items"], r["in_flight"]) in shapes and not r["cached"]
+    assert t.cfg.lookups_in_flight == r["in_flight"]
+    assert t.enumerate()[1] == 0  # restored to the empty table
+    st = t.insert(keys).cpu().numpy()
+    assert (st == P().PUT).all() and t.enumerate()[1] == n
+    r2 = tune_table(t, "insert", keys, reps=1)
+    assert r2["cached"] and r2["in_flight"] == r["in_flight"]

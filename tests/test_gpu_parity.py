@@ -145,7 +145,7 @@ def test_sequential_iceberg_bit_exact(T, geom):
 # --------------------------------------------------------------------------
 # concurrent cuckoo
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("T,items,P", [(4, 1, 1), (8, 2, 2), (16, 8, 4), (8, 5, 4), (4, 3, 2)])
+@pytest.mark.parametrize("T,items,P", [(4, 1, 1), (8, 2, 1), (16, 8, 1), (8, 1, 4), (4, 3, 4), (16, 1, 4), (8, 1, 8), (4, 1, 8), (16, 2, 8)])
 def test_cuckoo_2e14_fill_08_lookup_parity(T, items, P):
     """2^14 buckets x 48 slots, 32-bit keys, 629,145 keys (fill 0.8), then 2^20
     lookups, half present and half absent."""
@@ -180,9 +180,12 @@ def test_cuckoo_2e14_fill_08_lookup_parity(T, items, P):
     assert d.check_cuckoo_chain() == 0
 
 
-@pytest.mark.parametrize("compact", [True, False])
-def test_cuckoo_past_capacity_conserves_keys(compact):
-    t = cht().Table(cht().CUCKOO, 28, 1 << 10, compact=compact, max_chain=8, seed=3)
+@pytest.mark.parametrize("compact,P", [(True, 4), (False, 4), (True, 1), (True, 8)])
+def test_cuckoo_past_capacity_conserves_keys(compact, P):
+    """Puts past capacity (fill 0.99, C = 8): every key is stored or handed
+    back as dropped, for the stream put (P = 4, 8) and the chunk put (P = 1)."""
+    t = cht().Table(cht().CUCKOO, 28, 1 << 10, compact=compact, max_chain=8, seed=3,
+                    lookups_in_flight=P)
     n = int(0.99 * t.slots)
     keys = W.unique_keys(0, n, 28, 99)
     dropped = torch.zeros(n, dtype=torch.int64, device=DEV)
