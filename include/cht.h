@@ -87,8 +87,8 @@ typedef struct cht_table cht_table; /* opaque host handle */
  *                       (Algorithm 4); 0 = 128.
  * seed                  all permutation constants derive from it.
  * tile                  threads cooperating on one bucket: 4, 8 or 16; 0 lets
- *                       each operation use its fastest width (cuckoo puts 4,
- *                       everything else 8).
+ *                       each operation use its fastest width (cuckoo lookups
+ *                       8, everything else 4).
  * items_per_thread      keys each thread holds per work chunk, 1..8 (0 = 1);
  *                       iceberg operations use 1, 2 or 4 (larger values
  *                       count as 4, 3 as 2).
@@ -263,9 +263,11 @@ size_t cht_batch_scratch_bytes(int count);
  * Plan a batch: count (1..16384) entries of (tables[i], d_keys[i], n[i],
  * d_status[i]). The descriptors are written into the caller-owned device
  * scratch d_scratch (at least cht_batch_scratch_bytes(count) bytes, 16-byte
- * aligned) by a copy enqueued on stream; the scratch must stay untouched until
- * cht_batch_destroy. Launch shape: tile 8, 1 item per thread, 256 threads
- * per block unless changed with cht_batch_set_launch.
+ * aligned) by small kernels enqueued on stream (the descriptors travel as
+ * kernel parameters, so the call does not wait on the stream); the scratch
+ * must stay untouched until cht_batch_destroy. Launch shape: tile 4, 1 item
+ * per thread, 256 threads per block unless changed with
+ * cht_batch_set_launch.
  */
 int cht_batch_create(cht_table *const *tables, const void *const *d_keys, const size_t *n,
                      uint8_t *const *d_status, int count, int op, void *d_scratch,

@@ -163,18 +163,21 @@ void fill_level(Level &L, uint64_t *words, uint64_t nb, int key_bits, int fpw, u
 enum Op { kOpCuckooInsert, kOpCuckooFind, kOpIcebergFop, kOpIcebergFind };
 
 // threads per bucket for an operation: the configured tile, or when it is 0
-// the width measured fastest on GB300 for that operation (cuckoo puts keep
-// four lanes per bucket so that more puts are in flight; lookups use eight
-// lanes, one 16-byte read each, so one warp load fetches four whole lines)
+// the width measured fastest on GB300 for that operation. Cuckoo lookups use
+// eight lanes, one 16-byte read each, so one warp load fetches four whole
+// lines and their stream kernel keeps four of those in flight per tile.
+// Everything else keeps four lanes per bucket: twice the keys per warp pass,
+// which outweighs the second 16-byte read per lane for the puts and for the
+// iceberg engine's passes.
 int tile_for(const cht_table *t, Op op) {
     if (t->cfg.tile) return t->cfg.tile;
     switch (op) {
         case kOpCuckooInsert: return 4;
         case kOpCuckooFind: return 8;
-        case kOpIcebergFop: return 8;
-        case kOpIcebergFind: return 8;
+        case kOpIcebergFop: return 4;
+        case kOpIcebergFind: return 4;
     }
-    return 8;
+    return 4;
 }
 
 LaunchParams launch_params(const cht_table *t, void *stream) {
@@ -417,7 +420,7 @@ int batch_launch_params(const cht_batch *b, void *stream, LaunchParams &lp, int 
     lp.in_flight = 1;
     lp.sms = b->sms;
     lp.stream = static_cast<cudaStream_t>(stream);
-    T = b->launch.tile ? b->launch.tile : 8;
+    T = b->launch.tile ? b->launch.tile : 4;
     const uint64_t per = (uint64_t)32 * batch_items(lp.items);
     chunks = 0;
     for (const BatchDesc &d : b->host) chunks += (d.n + per - 1) / per;

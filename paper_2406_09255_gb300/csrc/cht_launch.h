@@ -79,7 +79,7 @@ cudaError_t launch_iceberg_warp(int T, int fpw0, bool lookup, const LaunchParams
 
 struct BatchDesc;
 // launch shape of the allocation-free fused find-or-put
-constexpr int kStaticBatchTile = 8;
+constexpr int kStaticBatchTile = 4;
 constexpr int kStaticBatchItems = 1;
 // keys per lane of the warp-batched engine for an items_per_thread setting:
 // 1, 2 or 4 (a warp takes chunks of 32 * I keys of one table)

@@ -24,6 +24,27 @@
 
 namespace cht {
 
+// field_op_issue / claim_finish with the packing known only at run time
+__device__ __forceinline__ uint64_t claim_issue_rt(int fpw, uint64_t *wp, int f, uint64_t snap,
+                                                   uint64_t entry, uint64_t &expected) {
+    switch (fpw) {
+        case 1: return field_op_issue<1>(false, wp, f, snap, entry, expected);
+        case 2: return field_op_issue<2>(false, wp, f, snap, entry, expected);
+        case 3: return field_op_issue<3>(false, wp, f, snap, entry, expected);
+        default: return field_op_issue<4>(false, wp, f, snap, entry, expected);
+    }
+}
+__device__ __forceinline__ bool claim_finish_rt(int fpw, uint64_t *wp, int f, uint64_t old,
+                                                uint64_t expected, uint64_t entry, uint64_t &seen,
+                                                int &fails) {
+    switch (fpw) {
+        case 1: return claim_finish<1>(wp, f, old, expected, entry, seen, fails);
+        case 2: return claim_finish<2>(wp, f, old, expected, entry, seen, fails);
+        case 3: return claim_finish<3>(wp, f, old, expected, entry, seen, fails);
+        default: return claim_finish<4>(wp, f, old, expected, entry, seen, fails);
+    }
+}
+
 // a warp's share of the keys: up to 32 * I keys of one table
 struct WarpChunk {
     const TableArgs *ta;
@@ -148,6 +169,10 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                     if (r[i] >= 0) load_relaxed<W>(p[i], v[i]);
                 }
                 more = false;
+                // claims of all I items are issued before any outcome is read
+                uint64_t old[I], expd[I];
+                int fei[I], cli[I];
+                uint32_t bmv = 0, bev = 0;
 #pragma unroll
                 for (int i = 0; i < I; ++i) {
                     more |= pm[i] != 0;
@@ -174,15 +199,31 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                         scan_chunk<W, FPW0>(v[i], e[i], m, fe);
                         const uint32_t bm = __ballot_sync(0xffffffffu, live && m) & tmask;
                         const uint32_t be = __ballot_sync(0xffffffffu, live && fe >= 0) & tmask;
-                        const int cl = be ? __ffs(be) - 1 - tbase : 0;
-                        bool claimed = false;
-                        uint64_t seen = 0;
-                        if (live && !bm && be && tl == cl)
-                            claimed = claim_field<FPW0>(const_cast<uint64_t *>(p[i]) + fe / FPW0,
-                                                        fe % FPW0, pick_word<W>(v[i], fe / FPW0),
-                                                        e[i], seen, n_fail);
-                        claimed = tile_shfl<T>(claimed, cl);
-                        seen = tile_shfl<T>(seen, cl);
+                        cli[i] = be ? __ffs(be) - 1 - tbase : 0;
+                        fei[i] = fe;
+                        bmv |= (bm ? 1u : 0u) << i;
+                        bev |= (be ? 1u : 0u) << i;
+                        old[i] = expd[i] = 0;
+                        if (live && !bm && be && tl == cli[i])
+                            old[i] = field_op_issue<FPW0>(
+                                false, const_cast<uint64_t *>(p[i]) + fe / FPW0, fe % FPW0,
+                                pick_word<W>(v[i], fe / FPW0), e[i], expd[i]);
+                    }
+                }
+                if constexpr (!LOOKUP) {
+#pragma unroll
+                    for (int i = 0; i < I; ++i) {
+                        const bool live = r[i] >= 0;
+                        const bool bm = (bmv >> i) & 1u, be = (bev >> i) & 1u;
+                        int outcome = 0;  // 1: written, 2: the same key won the slot, 0: lost
+                        if (live && !bm && be && tl == cli[i]) {
+                            uint64_t seen = 0;
+                            const bool won = claim_finish<FPW0>(
+                                const_cast<uint64_t *>(p[i]) + fei[i] / FPW0, fei[i] % FPW0, old[i],
+                                expd[i], e[i], seen, n_fail);
+                            outcome = won ? 1 : (seen == (uint64_t)e[i] ? 2 : 0);
+                        }
+                        outcome = tile_shfl<T>(outcome, cli[i]);
                         if (tl == r[i]) {
                             n_probe++;
                             if (bm) {
@@ -190,11 +231,11 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                                 pending[i] = false;
                             } else if (!be) {
                                 lvl2[i] = true;  // level 1 is full for good
-                            } else if (claimed) {
+                            } else if (outcome == 1) {
                                 st[i] = ST_PUT;
                                 pending[i] = false;
                                 n_write++;
-                            } else if (seen == (uint64_t)e[i]) {
+                            } else if (outcome == 2) {
                                 st[i] = ST_FOUND;  // another thread put k first
                                 pending[i] = false;
                             } else if (++it[i] > max_iter) {
