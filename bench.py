@@ -343,8 +343,9 @@ def oracle_sample(spec, n_ins, n_find, seed_index=None):
     return (n_ins + n_find) / dt / 1e6, dt
 
 
-def cpu_baseline(spec, budget_s=15.0):
-    # calibrate on a small sample, then size the measured one to ~budget_s
+def cpu_baseline(spec, budget_s=25.0):
+    # calibrate on a small sample, then size the measured one to ~budget_s; the
+    # small sample's rate runs about 2x low, so the measured run takes ~10-15 s
     rate, dt = oracle_sample(spec, 200_000, 1_300_000)
     total = int(max(1.5e6, min(2e8, rate * 1e6 * budget_s)))
     n_ins = total * 2 // 15

@@ -172,17 +172,19 @@ class Server:
             # form a wave: per table, a run of lookups or one write request
             budget = self._budget_keys()
             wave, used, taken, rest = [], 0, {}, []
+            blocked = set()  # tables with an earlier request left for a later wave
             for r in pending:
                 kind = "r" if r.op == FIND else "w"
                 cur = taken.get(r.table)
                 fits = used + r.n <= budget or not wave
                 ok = fits and (cur is None or (cur == "r" and kind == "r"))
-                if ok and not any(x.table == r.table for x in rest):
+                if ok and r.table not in blocked:
                     wave.append(r)
                     used += r.n
                     taken[r.table] = kind
                 else:
                     rest.append(r)
+                    blocked.add(r.table)
             pending = rest
             tnow = time.perf_counter() - t0
             for r in wave:
