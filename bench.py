@@ -538,6 +538,79 @@ def run_batch256(args, dev):
     print(json.dumps(out))
 
 
+def run_iceberg_variants(args, dev):
+    """Iceberg slot widths at equal slot counts (2^27 primary + 2^24 secondary
+    slots, 36-bit keys, 128-byte buckets): extra compact (16-bit primary,
+    32-bit secondary fields; 9/32 of the whole-key memory), compact (32/32;
+    1/2) and whole-key (64/64). Each is filled with find-or-put batches of
+    unique keys to 0.5 / 0.7 / 0.8 / 0.9 (the put benchmark), and after each
+    fill 2^26 lookups at 50 % hit are timed."""
+    from paper_2406_09255_gb300 import ICEBERG, Table
+    from paper_2406_09255_gb300 import workloads as W
+    w = 36
+    seed = W.SEED_BASE + 6
+    variants = [
+        ("extra_compact_16_32", dict(num_buckets=1 << 21, num_buckets_backyard=1 << 19,
+                                     fields_per_word=4, fields_per_word_backyard=2)),
+        ("compact_32_32", dict(num_buckets=1 << 22, num_buckets_backyard=1 << 19,
+                               fields_per_word=2, fields_per_word_backyard=2)),
+        ("whole_key_64_64", dict(num_buckets=1 << 23, num_buckets_backyard=1 << 20, compact=False)),
+    ]
+    fills = (0.5, 0.7, 0.8, 0.9)
+    nq = 1 << 26
+
+    def ev_ms(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    results = {}
+    for name, kw in variants:
+        nb, nb1 = kw.pop("num_buckets"), kw.pop("num_buckets_backyard")
+        t = Table(ICEBERG, w, nb, nb1, seed=6000, device=dev, **kw)
+        slots = t.slots
+        bounds = [0] + [int(f * slots) for f in fills]
+        keys = W.unique_keys(0, bounds[-1], w, seed, device=dev)
+        st = torch.empty(bounds[-1], dtype=torch.uint8, device=dev)
+        fst = torch.empty(nq, dtype=torch.uint8, device=dev)
+        rows = {f: {"put": [], "find": []} for f in fills}
+        full = 0
+        for rep in range(max(1, args.steps)):
+            t.clear()
+            torch.cuda.synchronize()
+            for i, f in enumerate(fills):
+                lo, hi = bounds[i], bounds[i + 1]
+                ms = ev_ms(lambda: t.find_or_put(keys[lo:hi], status=st[lo:hi]))
+                rows[f]["put"].append((hi - lo) / ms / 1e3)
+                q, _ = W.find_queries(hi, nq, 0.5, w, seed, bounds[-1], device=dev,
+                                      shuffle_seed=seed + i)
+                ms = ev_ms(lambda: t.find(q, status=fst))
+                rows[f]["find"].append(nq / ms / 1e3)
+                del q
+            full = int((st == 3).sum().item())
+        results[name] = {
+            "table_bytes": int(t.storage.numel()), "slots": slots, "full_puts": full,
+            "put_mops": {str(f): statistics.median(rows[f]["put"]) for f in fills},
+            "find50_mops": {str(f): statistics.median(rows[f]["find"]) for f in fills}}
+        del t, keys, st, fst
+        torch.cuda.empty_cache()
+    base = results["whole_key_64_64"]["table_bytes"]
+    for r in results.values():
+        r["memory_vs_whole_key"] = r["table_bytes"] / base
+    out = {"metric": "Mops/s iceberg put (find-or-put of unique keys) and find vs fill, by slot width",
+           "value": statistics.mean(results["extra_compact_16_32"]["put_mops"].values()),
+           "unit": "Mops/s", "n_gpus": 1, "higher_is_better": True, "dtype": "u64",
+           "data": "synthetic",
+           "config": {"workload": "iceberg_variants: 2^27 + 2^24 slots, 36-bit keys, 128-B "
+                                  "buckets; 16/32-bit, 32/32-bit and 64/64-bit slots; fills "
+                                  "0.5/0.7/0.8/0.9; 2^26 lookups at 50% hit per fill"},
+           "results": results}
+    print(json.dumps(out))
+
+
 def run_served(args, dev):
     """16 resident compact iceberg tables (48-bit keys, 2^20..2^23 primary
     buckets), Poisson request arrivals at rates relative to the saturated
@@ -653,7 +726,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     others = {"iceberg_stream": run_iceberg_stream, "batch256": run_batch256,
-              "served": run_served}
+              "served": run_served, "iceberg_variants": run_iceberg_variants}
     ap.add_argument("--workload", default="cuckoo_2e24", choices=sorted(WORKLOADS) + sorted(others))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
