@@ -23,6 +23,7 @@ a reference implementation, which the paper does not ship).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -254,6 +255,44 @@ class Workload:
                 res[("found", fi, hi)] = found
         t.detach_counters()
         return res
+
+
+def random_read_ceiling(dev, block_bytes=128, n_blocks=1 << 28, buf_bytes=1 << 31):
+    """Random-access rate of device memory (blocks per second) measured with
+    cht_random_read: the ceiling for bucket probes."""
+    from paper_2406_09255_gb300 import _lib
+    L = _lib.load()
+    buf = torch.empty(buf_bytes, dtype=torch.uint8, device=dev)
+    buf.fill_(1)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    s = torch.cuda.current_stream(dev)
+    times = []
+    for rep in range(4):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        _lib.check(L.cht_random_read(buf.data_ptr(), buf.numel(), block_bytes, n_blocks, rep,
+                                     sink.data_ptr(), ctypes.c_void_p(s.cuda_stream)))
+        b.record(s)
+        torch.cuda.synchronize(dev)
+        if rep:
+            times.append(a.elapsed_time(b))
+    del buf
+    return n_blocks / (statistics.median(times) * 1e-3)
+
+
+def run_random_read(args, dev):
+    """Random-access rate of HBM by block size (cht_random_read over a 2 GiB
+    buffer, and over a 32 MiB L2-resident one): the ceiling behind every
+    bucket probe."""
+    out = {"metric": "random block reads per second by block size", "unit": "G blocks/s",
+           "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "results": {}}
+    for bb in (32, 64, 128, 256):
+        r = random_read_ceiling(dev, block_bytes=bb)
+        out["results"][f"hbm_{bb}B"] = {"g_blocks_per_s": r / 1e9, "gbs": r * bb / 1e9}
+    r = random_read_ceiling(dev, block_bytes=128, buf_bytes=1 << 25)
+    out["results"]["l2_128B"] = {"g_blocks_per_s": r / 1e9, "gbs": r * 128 / 1e9}
+    out["value"] = out["results"]["hbm_128B"]["g_blocks_per_s"]
+    print(json.dumps(out))
 
 
 def run_e2e(wl, steps, warmup):
@@ -726,7 +765,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     others = {"iceberg_stream": run_iceberg_stream, "batch256": run_batch256,
-              "served": run_served, "iceberg_variants": run_iceberg_variants}
+              "served": run_served, "iceberg_variants": run_iceberg_variants,
+              "random_read": run_random_read}
     ap.add_argument("--workload", default="cuckoo_2e24", choices=sorted(WORKLOADS) + sorted(others))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -795,7 +835,7 @@ def main():
     peak, peak_kind = peaks()
 
     # roofline of the lookup kernel: sum of algorithmic bytes / sum of durations
-    fb, fms, fq = 0.0, 0.0, 0
+    fb, fms, fq, fprobes = 0.0, 0.0, 0, 0.0
     phases = []
     for fi, f in enumerate(spec["fills"]):
         n_ins = wl.n_f[fi] - (wl.n_f[fi - 1] if fi else 0)
@@ -809,6 +849,7 @@ def main():
             p, _, _, ops = counts[("find", fi, hi)]
             by = 128.0 * p + 9.0 * wl.nq
             fb += by * len(ph[("find", fi, hi)])
+            fprobes += p * len(ph[("find", fi, hi)])
             fms += sum(ph[("find", fi, hi)])
             fq += wl.nq * len(ph[("find", fi, hi)])
             entry[f"find{int(h * 100)}_mops"] = wl.nq / fms_i / 1e3
@@ -817,12 +858,19 @@ def main():
             entry[f"find{int(h * 100)}_found"] = counts[("found", fi, hi)]
         phases.append(entry)
     achieved = fb / (fms * 1e-3) / 1e9
+    ceiling = random_read_ceiling(dev)
+    probe_rate = fprobes / (fms * 1e-3)
     launches = len([1 for k in ph if k[0] == "find"])
     tpu = traffic_per_unit("cuckoo_find")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": (tpu * wl.nq) if tpu else None,
                 "kernel": "k_cuckoo_find_stream<8,3,4>", "peak_source": f"{peak_kind} hbm_gbs",
-                "algorithmic_bytes_per_launch": fb / (fq / wl.nq)}
+                "algorithmic_bytes_per_launch": fb / (fq / wl.nq),
+                "random_access": {"probes_per_s": probe_rate,
+                                  "ceiling_lines_per_s": ceiling,
+                                  "frac_of_ceiling": probe_rate / ceiling if ceiling else None,
+                                  "ceiling_source": "cht_random_read: 2^28 random 128-byte "
+                                                    "line reads over a 2 GiB buffer, median of 3"}}
 
     e2e = None
     if not args.no_e2e:

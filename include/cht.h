@@ -329,6 +329,22 @@ const char *cht_last_error(void);
 /* Library version string. */
 const char *cht_version(void);
 
+/*
+ * Measurement utility; the paper has no counterpart. Reads n_blocks blocks of
+ * block_bytes (32, 64, 128 or 256) from d_buf at pseudo-random block indices
+ * (splitmix64 of seed + i, masked to the block count) and XOR-folds the data
+ * into *d_sink. One tile of lanes reads a block with one 16-byte (256: 32-byte)
+ * load per lane, four blocks in flight per tile, on a grid that fills the
+ * GPU. Timed with events on stream, it gives the random-access rate of the
+ * memory behind d_buf: the ceiling for bucket probes, which are reads of one
+ * 128-byte line at a data-dependent address. d_buf: device memory of
+ * buf_bytes = block_bytes x a power of two, 32-byte aligned, only read;
+ * d_sink: one 8-byte aligned device word, modified. Asynchronous on stream;
+ * CHT_ERR_INVALID on bad arguments, CHT_ERR_CUDA if the launch fails.
+ */
+int cht_random_read(const void *d_buf, size_t buf_bytes, int block_bytes, uint64_t n_blocks,
+                    uint64_t seed, uint64_t *d_sink, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,8 @@ SIGNATURES = {
                                                     ctypes.POINTER(_vp), ctypes.c_int, _vp]),
     "cht_last_error": (ctypes.c_char_p, []),
     "cht_version": (ctypes.c_char_p, []),
+    "cht_random_read": (ctypes.c_int, [_vp, _sz, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                       _vp, _vp]),
 }
 
 _lock = threading.Lock()

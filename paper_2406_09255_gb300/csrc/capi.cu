@@ -391,6 +391,26 @@ const char *cht_last_error(void) { return g_err.c_str(); }
 
 const char *cht_version(void) { return "cht 0.1 (sm_103a)"; }
 
+int cht_random_read(const void *d_buf, size_t buf_bytes, int block_bytes, uint64_t n_blocks,
+                    uint64_t seed, uint64_t *d_sink, void *stream) {
+    if (block_bytes != 32 && block_bytes != 64 && block_bytes != 128 && block_bytes != 256)
+        return fail(CHT_ERR_INVALID, "block_bytes must be 32, 64, 128 or 256");
+    if (!d_buf || !d_sink) return fail(CHT_ERR_INVALID, "null buffer");
+    if ((reinterpret_cast<uintptr_t>(d_buf) % 32) || (reinterpret_cast<uintptr_t>(d_sink) % 8))
+        return fail(CHT_ERR_INVALID, "d_buf must be 32-byte and d_sink 8-byte aligned");
+    if (buf_bytes % (size_t)block_bytes || !is_pow2(buf_bytes / (size_t)block_bytes))
+        return fail(CHT_ERR_INVALID, "buf_bytes must be block_bytes times a power of two");
+    if (n_blocks == 0) return ok();
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = launch_random_read(d_buf, buf_bytes, block_bytes, n_blocks, seed,
+                               reinterpret_cast<unsigned long long *>(d_sink), sms,
+                               static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "random read kernel launch");
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -66,6 +66,9 @@ inline int grid_blocks_warp(const void *kern, const LaunchParams &lp, uint64_t n
     return b < 1 ? 1 : (int)b;
 }
 
+cudaError_t launch_random_read(const void *buf, size_t buf_bytes, int block_bytes,
+                               uint64_t n_blocks, uint64_t seed, unsigned long long *sink,
+                               int sms, cudaStream_t stream);
 cudaError_t launch_cuckoo_insert(int T, int fpw, const LaunchParams &lp, const TableArgs &ta,
                                  const void *keys, uint64_t n, uint8_t *status,
                                  uint64_t *dropped);

@@ -107,3 +107,17 @@ def test_invalid_configs_rejected_with_message(lib, kw, frag):
 
 def test_version(lib):
     assert b"sm_103a" in lib.load().cht_version()
+
+
+def test_random_read_rejects_bad_arguments_without_a_launch(lib):
+    """cht_random_read validates on the host before any CUDA call."""
+    L = lib.load()
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails validation
+    sink = ctypes.c_void_p(1 << 21)
+    assert L.cht_random_read(fake, 1 << 20, 100, 10, 0, sink, None) == lib.CHT_ERR_INVALID
+    assert "block_bytes" in L.cht_last_error().decode()
+    assert L.cht_random_read(None, 1 << 20, 128, 10, 0, sink, None) == lib.CHT_ERR_INVALID
+    assert L.cht_random_read(fake, 3 * 128, 128, 10, 0, sink, None) == lib.CHT_ERR_INVALID
+    assert "power of two" in L.cht_last_error().decode()
+    assert L.cht_random_read(ctypes.c_void_p((1 << 20) + 8), 1 << 20, 128, 10, 0, sink,
+                             None) == lib.CHT_ERR_INVALID

@@ -391,3 +391,41 @@ def test_cuckoo_2e24_full_size_sampled():
     qs = q[idx.to(DEV)].cpu().numpy().view(np.uint64)
     assert (d.find(qs) == got[idx.to(DEV)].cpu().numpy()).all()
     assert d.check_prefix() == 0
+
+
+def test_random_read_utility_reads_every_block_size():
+    """cht_random_read (a measurement utility) reads the blocks it should:
+    over a buffer of seeded random words, the XOR-fold of every lane's word
+    sums equals the value recomputed here from the block indices (splitmix64
+    of seed + i * golden-ratio increment, masked to the block count)."""
+    import ctypes
+    from paper_2406_09255_gb300 import _lib
+    L = _lib.load()
+    nwords = 1 << 22  # 32 MiB of seeded random words
+    host = np.random.default_rng(11).integers(0, 1 << 63, nwords, dtype=np.int64).view(np.uint64)
+    buf = torch.from_numpy(host.view(np.int64)).to(DEV)
+    M = (1 << 64) - 1
+
+    def mix(z):
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9))
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB))
+        return z ^ (z >> np.uint64(31))
+
+    n, seed = 1 << 16, 7
+    for bb, lanes, bpl in ((32, 2, 16), (64, 4, 16), (128, 8, 16), (256, 8, 32)):
+        sink = torch.zeros(1, dtype=torch.int64, device=DEV)
+        _lib.check(L.cht_random_read(buf.data_ptr(), nwords * 8, bb, n, seed,
+                                     sink.data_ptr(), None))
+        torch.cuda.synchronize()
+        with np.errstate(over="ignore"):
+            i = np.arange(n, dtype=np.uint64)
+            blk = mix(np.uint64(seed) + i * np.uint64(0x9E3779B97F4A7C15)) & np.uint64(nwords * 8 // bb - 1)
+            want = np.uint64(0)
+            per = bpl // 8
+            for lane in range(lanes):
+                base = (blk * np.uint64(bb // 8) + np.uint64(lane * per)).astype(np.int64)
+                tot = np.zeros(n, dtype=np.uint64)
+                for k in range(per):
+                    tot += host[base + k]
+                want ^= np.bitwise_xor.reduce(tot)
+        assert (int(sink.item()) & M) == int(want), bb
