@@ -95,6 +95,7 @@ def lib():
                 "orc_iceberg_fop": (None, [_cfgp, _u64p, _u64p, _u64p, _sz, _u8p, _u64p, _u64p]),
                 "orc_iceberg_find": (None, [_cfgp, _u64p, _u64p, _u64p, _sz, _u8p, _u64p]),
                 "orc_enumerate": (u64, [_cfgp, _u64p, _u64p, _u64p, u64]),
+                "orc_iceberg_locate": (None, [_cfgp, _u64p, _u64p, _u64p, _sz, _u64p]),
                 "orc_check_prefix": (u64, [_cfgp, i, _u64p]),
                 "orc_check_entries": (u64, [_cfgp, _u64p, _u64p]),
                 "orc_check_order_property": (u64, [_cfgp, _u64p, _u64p]),
@@ -229,6 +230,16 @@ class Table:
                                    _p8(st), ctypes.byref(p))
         self.probes = p.value
         return st
+
+    def locate(self, keys) -> np.ndarray:
+        """Slot index of each key (iceberg): a * B0 + y at level 0,
+        nb0 * B0 + a * B1 + y at level 1; 2^64 - 1 if absent or invalid."""
+        assert self.cfg.kind == ICEBERG
+        k = _keys(keys)
+        out = np.zeros(len(k), dtype=np.uint64)
+        lib().orc_iceberg_locate(self._cp, _p64(self.t0), _p64(self.t1), _p64(k), len(k),
+                                 _p64(out))
+        return out
 
     def find_exhaustive(self, keys):
         assert self.cfg.kind == CUCKOO

@@ -516,6 +516,42 @@ void orc_iceberg_find(const orc_cfg *c, const uint64_t *t0, const uint64_t *t1,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Slot index of a stored key (iceberg entries never move, Section 5.1, so   */
+/* the index can address a value array: the key-value extension)            */
+/* ------------------------------------------------------------------------ */
+
+/* Level-0 slots are numbered a * B0 + y, level-1 slots nb0 * B0 + a * B1 + y,
+ * with y the slot's position in bucket a. Absent or invalid keys get
+ * UINT64_MAX. */
+void orc_iceberg_locate(const orc_cfg *c, const uint64_t *t0, const uint64_t *t1,
+                        const uint64_t *keys, size_t n, uint64_t *slot_out)
+{
+    int B0 = orc_slots_per_bucket(c, 0);
+    int B1 = c->kind == 1 ? orc_slots_per_bucket(c, 1) : 0;
+    for (size_t i = 0; i < n; i++) {
+        uint64_t k = keys[i];
+        slot_out[i] = UINT64_MAX;
+        if (!orc_valid_key(c, k))
+            continue;
+        for (int x = 0; x <= 2 && slot_out[i] == UINT64_MAX; x++) {
+            int level = x == 0 ? 0 : 1;
+            uint64_t a = orc_iceberg_bucket(c, x, k);
+            uint64_t e = orc_iceberg_entry(c, x, k);
+            const uint64_t *t = orc_level_table(x, t0, t1);
+            int B = level == 0 ? B0 : B1;
+            for (int y = 0; y < B; y++) {
+                if (orc_get_slot(c, level, t, a, y) == e) {
+                    slot_out[i] = level == 0
+                                      ? a * (uint64_t)B0 + (uint64_t)y
+                                      : c->nb[0] * (uint64_t)B0 + a * (uint64_t)B1 + (uint64_t)y;
+                    break;
+                }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Enumerate: k = pi^-1(a . r) for every stored entry (Section 2.4)          */
 /* ------------------------------------------------------------------------ */
 

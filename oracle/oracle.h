@@ -97,6 +97,11 @@ void orc_iceberg_fop(const orc_cfg *c, uint64_t *t0, uint64_t *t1,
 void orc_iceberg_find(const orc_cfg *c, const uint64_t *t0, const uint64_t *t1,
                       const uint64_t *keys, size_t n, uint8_t *status,
                       uint64_t *probes);
+/* Slot index of each key in an iceberg table: level-0 slot y of bucket a is
+ * a * B0 + y, level-1 slot y of bucket a is nb0 * B0 + a * B1 + y (B = slots
+ * per bucket of the level); UINT64_MAX for absent or invalid keys. */
+void orc_iceberg_locate(const orc_cfg *c, const uint64_t *t0, const uint64_t *t1,
+                        const uint64_t *keys, size_t n, uint64_t *slot_out);
 /* Decode every stored entry back to its key (k = pi^-1(a . r)). Writes at
  * most cap keys, returns the number of stored entries. */
 uint64_t orc_enumerate(const orc_cfg *c, const uint64_t *t0,

@@ -221,3 +221,49 @@ def test_invalid_keys():
     st = t.insert(np.array([0, 1 << 20, 5, (1 << 20) - 1], dtype=np.uint64))
     assert list(st) == [INVALID, INVALID, PUT, PUT]
     assert list(t.find(np.array([0, 5, 1 << 21], dtype=np.uint64))) == [INVALID, FOUND, INVALID]
+
+
+@pytest.mark.parametrize("wpb,f0,f1", [(16, 2, 2), (4, 3, 1), (2, 4, 2)])
+def test_locate_closed_form_single_buckets(wpb, f0, f1):
+    """Slot index (the key-value extension's handle), pinned by a closed form:
+    with one primary and one secondary bucket, sequential puts fill the
+    primary's slots in slot order (first empty slot, Algorithm 1), so the i-th
+    key sits at slot i; the next B1 keys go to the one secondary bucket, whose
+    slots follow the primary level's B0 slots. Keys past B0 + B1 are FULL and
+    located nowhere."""
+    w = 15  # remainders of 15 bits fit every packing here, 16-bit slots included
+    t = oracle.Table(oracle.ICEBERG, w, 1, 1, wpb=wpb, fpw0=f0, fpw1=f1, seed=5)
+    B0, B1 = t.slots_per_bucket(0), t.slots_per_bucket(1)
+    assert B0 == wpb * f0 and B1 == wpb * f1
+    keys = np.arange(1, B0 + B1 + 4, dtype=np.uint64) * np.uint64(211)
+    assert int(keys.max()) < (1 << w)
+    st = t.find_or_put(keys)
+    assert (st[: B0 + B1] == oracle.PUT).all() and (st[B0 + B1:] == oracle.FULL).all()
+    got = t.locate(keys)
+    want = np.concatenate([np.arange(B0 + B1, dtype=np.uint64),
+                           np.full(3, np.iinfo(np.uint64).max, dtype=np.uint64)])
+    assert np.array_equal(got, want)
+    # the located slot holds the key's own entry: r'_0 at level 0, r'_{1+i} at level 1
+    for k, s in zip(keys[: B0 + B1].tolist(), got[: B0 + B1].tolist()):
+        if s < B0:
+            assert t.slot(0, 0, s) == (t.remainder(0, 0, k) << 1) | 1
+        else:
+            e = t.slot(1, 0, s - B0)
+            i = (e & 3) - 1
+            assert e >> 2 == t.remainder(1, i, k)
+
+
+def test_locate_bucket_offsets():
+    """Level-0 slot indices are a * B0 + y for the key's primary bucket a;
+    absent and invalid keys locate to 2^64 - 1."""
+    w = 32
+    t = oracle.Table(oracle.ICEBERG, w, 1 << 6, 1 << 3, fpw0=2, fpw1=2, seed=9)
+    B0 = t.slots_per_bucket(0)
+    keys = np.arange(1, 400, dtype=np.uint64) * np.uint64(104729)
+    assert (t.find_or_put(keys) == oracle.PUT).all()
+    got = t.locate(keys)
+    for k, s in zip(keys.tolist(), got.tolist()):
+        a = t.address(0, 0, k)
+        assert a * B0 <= s < (a + 1) * B0  # nothing spilled at this load
+    absent = t.locate(np.array([0, 3, 1 << 40], dtype=np.uint64))
+    assert (absent == np.iinfo(np.uint64).max).all()
