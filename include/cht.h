@@ -213,6 +213,44 @@ int cht_find_or_put(cht_table *t, const void *d_keys, size_t n,
                     uint8_t *d_status, void *stream);
 
 /*
+ * Key-value extension (the paper names a key-value map as the natural next
+ * step; iceberg entries never move once placed, Section 5.1, so a key's slot
+ * is a stable handle that can index a caller-owned value array).
+ *
+ * cht_find_or_put_slots: cht_find_or_put, and also d_slots[i] = the slot that
+ * holds key i after the call when its status is FOUND or PUT, else
+ * UINT64_MAX. cht_find_slots: cht_find, with d_slots as above for FOUND keys.
+ * Slot numbering: level-0 slot y of primary bucket a is a * B0 + y; level-1
+ * slot y of secondary bucket a is nb0 * B0 + a * B1 + y, where B0 = 16 *
+ * fields_per_word and B1 = 16 * fields_per_word_backyard are the slots per
+ * bucket and y runs over a bucket's slots in slot order (word by word, field
+ * by field). There are nb0 * B0 + nb1 * B1 slots in all. A key keeps its slot
+ * for the table's lifetime (until cht_clear). d_slots: n device uint64
+ * (8-byte aligned), written. Iceberg tables only (CHT_ERR_UNSUPPORTED on
+ * cuckoo tables, whose puts move entries); other arguments and errors as for
+ * cht_find_or_put / cht_find.
+ */
+int cht_find_or_put_slots(cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
+                          uint64_t *d_slots, void *stream);
+int cht_find_slots(const cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
+                   uint64_t *d_slots, void *stream);
+
+/*
+ * Value moves for the key-value extension. d_store is a caller-owned device
+ * array of store_slots values (value_bytes = 4, 8 or 16 each), indexed by slot.
+ * cht_values_scatter: d_store[d_slots[i]] = d_values[i] for every i with
+ * d_slots[i] < store_slots (two keys of one call with the same slot: one of
+ * the values lands, which one is unspecified). cht_values_gather: d_out[i] =
+ * d_store[d_slots[i]], or zero when d_slots[i] >= store_slots (UINT64_MAX for
+ * keys not found). d_slots: n device uint64; values aligned to value_bytes.
+ * Asynchronous on stream; CHT_ERR_INVALID on bad arguments.
+ */
+int cht_values_scatter(const uint64_t *d_slots, size_t n, const void *d_values, int value_bytes,
+                       void *d_store, uint64_t store_slots, void *stream);
+int cht_values_gather(const uint64_t *d_slots, size_t n, const void *d_store, int value_bytes,
+                      uint64_t store_slots, void *d_out, void *stream);
+
+/*
  * Write every stored key, decoded as k = pi_j^-1(a . r) (Section 2.4), to
  * d_out (key_bytes each) in unspecified order, at most cap keys. *d_count (a
  * device uint64) receives the number of stored keys, which may exceed cap;

@@ -8,3 +8,4 @@ library libcht.so (include/cht.h); this package is its Python binding.
 from ._lib import (CUCKOO, ERROR, FOUND, FULL, ICEBERG, INVALID, NOT_FOUND, PUT,  # noqa: F401
                    ChtError)
 from .table import Table, resolve_config, table_bytes  # noqa: F401
+from .kv import KVMap  # noqa: F401

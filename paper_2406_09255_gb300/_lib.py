@@ -86,6 +86,10 @@ SIGNATURES = {
     "cht_version": (ctypes.c_char_p, []),
     "cht_random_read": (ctypes.c_int, [_vp, _sz, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                        _vp, _vp]),
+    "cht_find_or_put_slots": (ctypes.c_int, [_vp, _vp, _sz, _vp, _vp, _vp]),
+    "cht_find_slots": (ctypes.c_int, [_vp, _vp, _sz, _vp, _vp, _vp]),
+    "cht_values_scatter": (ctypes.c_int, [_vp, _sz, _vp, ctypes.c_int, _vp, ctypes.c_uint64, _vp]),
+    "cht_values_gather": (ctypes.c_int, [_vp, _sz, _vp, ctypes.c_int, ctypes.c_uint64, _vp, _vp]),
 }
 
 _lock = threading.Lock()

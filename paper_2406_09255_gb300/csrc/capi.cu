@@ -336,6 +336,61 @@ int cht_find(const cht_table *t, const void *d_keys, size_t n, uint8_t *d_status
     return ce == cudaSuccess ? ok() : cuda_fail(ce, "find kernel launch");
 }
 
+int cht_find_or_put_slots(cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
+                          uint64_t *d_slots, void *stream) {
+    int e = check_keys(t, d_keys, n, d_status);
+    if (e) return e;
+    if (t->cfg.kind != CHT_ICEBERG)
+        return fail(CHT_ERR_UNSUPPORTED, "slot indices are stable in iceberg tables only");
+    if (!d_slots || (uintptr_t)d_slots % 8) return fail(CHT_ERR_INVALID, "d_slots must be 8-byte aligned");
+    if (n == 0) return ok();
+    const LaunchParams lp = launch_params(t, stream);
+    cudaError_t ce = launch_iceberg(tile_for(t, kOpIcebergFop), t->cfg.fields_per_word, false, lp,
+                                    t->args, d_keys, n, d_status, d_slots);
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "find-or-put kernel launch");
+}
+
+int cht_find_slots(const cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
+                   uint64_t *d_slots, void *stream) {
+    int e = check_keys(t, d_keys, n, d_status);
+    if (e) return e;
+    if (t->cfg.kind != CHT_ICEBERG)
+        return fail(CHT_ERR_UNSUPPORTED, "slot indices are stable in iceberg tables only");
+    if (!d_slots || (uintptr_t)d_slots % 8) return fail(CHT_ERR_INVALID, "d_slots must be 8-byte aligned");
+    if (n == 0) return ok();
+    const LaunchParams lp = launch_params(t, stream);
+    cudaError_t ce = launch_iceberg(tile_for(t, kOpIcebergFind), t->cfg.fields_per_word, true, lp,
+                                    t->args, d_keys, n, d_status, d_slots);
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "find kernel launch");
+}
+
+static int values_call(bool scatter, const uint64_t *d_slots, size_t n, const void *src,
+                       void *dst, int value_bytes, uint64_t store_slots, void *stream) {
+    if (value_bytes != 4 && value_bytes != 8 && value_bytes != 16)
+        return fail(CHT_ERR_INVALID, "value_bytes must be 4, 8 or 16");
+    if (n == 0) return ok();
+    if (!d_slots || !src || !dst) return fail(CHT_ERR_INVALID, "null pointer");
+    if ((uintptr_t)d_slots % 8 || (uintptr_t)src % value_bytes || (uintptr_t)dst % value_bytes)
+        return fail(CHT_ERR_INVALID, "misaligned slots or values");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = launch_values(scatter, d_slots, n, src, dst, value_bytes, store_slots, sms,
+                          static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "value kernel launch");
+}
+
+int cht_values_scatter(const uint64_t *d_slots, size_t n, const void *d_values, int value_bytes,
+                       void *d_store, uint64_t store_slots, void *stream) {
+    return values_call(true, d_slots, n, d_values, d_store, value_bytes, store_slots, stream);
+}
+
+int cht_values_gather(const uint64_t *d_slots, size_t n, const void *d_store, int value_bytes,
+                      uint64_t store_slots, void *d_out, void *stream) {
+    return values_call(false, d_slots, n, d_store, d_out, value_bytes, store_slots, stream);
+}
+
 int cht_find_or_put(cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
                     void *stream) {
     int e = check_keys(t, d_keys, n, d_status);

@@ -326,6 +326,31 @@ __device__ __forceinline__ void probe_chunk(const uint64_t (&v)[W], uint64_t ent
     last_empty = Fields<FPW>::get(v[W - 1], FPW - 1) == 0;
 }
 
+// local field index (word * FPW + field) of the owned field equal to entry,
+// or -1: the lowest flagged field of the first word with a flag is exact
+// (see Swar), and a table holds an entry at most once
+template <int W, int FPW>
+__device__ __forceinline__ int match_field(const uint64_t (&v)[W], uint64_t entry) {
+    using Z = Swar<FPW>;
+    const uint64_t pat = Z::spread(entry);
+    int r = -1;
+#pragma unroll
+    for (int i = W - 1; i >= 0; --i) {
+        const uint64_t z = Z::zeros(v[i] ^ pat);
+        if (z) r = i * FPW + (__ffsll((long long)z) - 1) / Z::S;
+    }
+    return r;
+}
+template <int W>
+__device__ __forceinline__ int match_field_rt(const uint64_t (&v)[W], uint64_t entry, int fpw) {
+    switch (fpw) {
+        case 1: return match_field<W, 1>(v, entry);
+        case 2: return match_field<W, 2>(v, entry);
+        case 3: return match_field<W, 3>(v, entry);
+        default: return match_field<W, 4>(v, entry);
+    }
+}
+
 // the same with the packing known only at run time (fpw in 1..4)
 template <int W>
 __device__ __forceinline__ void scan_chunk_rt(const uint64_t (&v)[W], uint64_t entry, int fpw,

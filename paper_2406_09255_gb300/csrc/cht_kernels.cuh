@@ -400,6 +400,7 @@ struct SingleWork : TileWork<T> {
     const void *keys;
     uint64_t n;
     uint8_t *status;
+    uint64_t *slots;  // optional slot index per key (iceberg key-value handle)
     __device__ __forceinline__ const TableArgs &ta() const { return *tap; }
     __device__ __forceinline__ void next() { this->refill(keys, tap->key_bytes, n, status); }
 };
@@ -466,6 +467,18 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
         const uint32_t be0 = tile_ballot<T>(p1 && f0 >= 0);
         const uint32_t bea = tile_ballot<T>(p2 && fa >= 0);
         const uint32_t beb = tile_ballot<T>(p2 && fb >= 0);
+        // where a match sits (slot outputs only): the first matching lane and
+        // its local field, and whether it is in secondary bucket b
+        int mlane = 0, mloc = -1;
+        bool min_b = false;
+        if (tw.slots) {
+            const uint32_t bma = tile_ballot<T>(p2 && ma);
+            const int ml = p1 ? match_field<W, FPW0>(v0, e0)
+                              : (ma ? match_field_rt<W>(va, ea, FPW1) : match_field_rt<W>(vb, eb, FPW1));
+            min_b = p2 && !bma;
+            mlane = bfound ? __ffs(bfound) - 1 : 0;
+            mloc = tile_shfl<T>(ml, mlane);
+        }
         // first empty slot index of each snapshot (B1 if none)
         const int la0 = be0 ? __ffs(be0) - 1 : 0;
         const int laa = bea ? __ffs(bea) - 1 : 0;
@@ -504,6 +517,8 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
         }
         claimed = tile_shfl<T>(claimed, cl);
         seen = tile_shfl<T>(seen, cl);
+        int cloc = 0;  // the claimed slot's local field in lane cl (slot outputs only)
+        if (tw.slots) cloc = tile_shfl<T>(lvl == 1 ? f0 : (pick_a ? fa : fb), cl);
 
         if (act) {
             bool fin = true;
@@ -544,6 +559,25 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
                     tw.s_st[tw.q] = st;
                     if (st == ST_ERROR) atomicOr(ta.err, 1u);
                     n_ops++;
+                    if (tw.slots) {
+                        // FOUND by a match: the matching slot; PUT, or FOUND
+                        // after losing the claim to k itself: the claimed slot
+                        const uint64_t B0 = (uint64_t)kWordsPerBucket * FPW0;
+                        uint64_t slot = ~0ull;
+                        if (st == ST_FOUND || st == ST_PUT) {
+                            const bool bym = st == ST_FOUND && bfound;
+                            const int ln = bym ? mlane : cl;
+                            const int loc = bym ? mloc : cloc;
+                            if (lvl == 1) {
+                                slot = q0.a * B0 + (uint64_t)(ln * W * FPW0 + loc);
+                            } else {
+                                const bool inb = bym ? min_b : !pick_a;
+                                slot = L0.nb * B0 + (inb ? qb.a : qa.a) * (uint64_t)B1 +
+                                       (uint64_t)(ln * LF1 + loc);
+                            }
+                        }
+                        tw.slots[tw.base + tw.q] = slot;
+                    }
                 }
                 tw.q++;
                 fresh = true;
@@ -563,7 +597,7 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
 template <int T, int FPW0, bool LOOKUP>
 __global__ void __launch_bounds__(256)
     k_iceberg(TableArgs ta, const void *__restrict__ keys, uint64_t n,
-              uint8_t *__restrict__ status, int items) {
+              uint8_t *__restrict__ status, uint64_t *__restrict__ slots, int items) {
     extern __shared__ uint64_t smem[];
     SingleWork<T> tw;
     tw.init(smem, reinterpret_cast<uint8_t *>(smem + (size_t)blockDim.x * items), items, n,
@@ -572,6 +606,7 @@ __global__ void __launch_bounds__(256)
     tw.keys = keys;
     tw.n = n;
     tw.status = status;
+    tw.slots = slots;
     iceberg_engine<T, FPW0, LOOKUP>(tw, ta.ctr);
 }
 

@@ -66,6 +66,9 @@ inline int grid_blocks_warp(const void *kern, const LaunchParams &lp, uint64_t n
     return b < 1 ? 1 : (int)b;
 }
 
+cudaError_t launch_values(bool scatter, const uint64_t *slots, uint64_t n, const void *src,
+                          void *dst, int value_bytes, uint64_t nslots, int sms,
+                          cudaStream_t stream);
 cudaError_t launch_random_read(const void *buf, size_t buf_bytes, int block_bytes,
                                uint64_t n_blocks, uint64_t seed, unsigned long long *sink,
                                int sms, cudaStream_t stream);
@@ -74,11 +77,17 @@ cudaError_t launch_cuckoo_insert(int T, int fpw, const LaunchParams &lp, const T
                                  uint64_t *dropped);
 cudaError_t launch_cuckoo_find(int T, int fpw, const LaunchParams &lp, const TableArgs &ta,
                                const void *keys, uint64_t n, uint8_t *status);
+// slots (nullable): per-key slot index output of iceberg operations
 cudaError_t launch_iceberg(int T, int fpw0, bool lookup, const LaunchParams &lp,
-                           const TableArgs &ta, const void *keys, uint64_t n, uint8_t *status);
+                           const TableArgs &ta, const void *keys, uint64_t n, uint8_t *status,
+                           uint64_t *slots = nullptr);
 cudaError_t launch_iceberg_warp(int T, int fpw0, bool lookup, const LaunchParams &lp,
                                 const TableArgs &ta, const void *keys, uint64_t n,
-                                uint8_t *status);
+                                uint8_t *status, uint64_t *slots = nullptr);
+// the warp-batched engine with slot outputs (one key per lane)
+cudaError_t launch_iceberg_warp_slots(int T, int fpw0, bool lookup, const LaunchParams &lp,
+                                      const TableArgs &ta, const void *keys, uint64_t n,
+                                      uint8_t *status, uint64_t *slots);
 
 struct BatchDesc;
 // launch shape of the allocation-free fused find-or-put

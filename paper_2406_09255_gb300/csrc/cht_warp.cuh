@@ -50,6 +50,7 @@ struct WarpChunk {
     const TableArgs *ta;
     const void *keys;
     uint8_t *status;
+    uint64_t *slots;  // optional slot index per key (iceberg key-value handle)
     uint64_t base;
     int count;
 };
@@ -59,13 +60,14 @@ struct SingleSource {
     const TableArgs *ta;
     const void *keys;
     uint8_t *status;
+    uint64_t *slots;
     uint64_t n;
     uint64_t per;  // keys per chunk
     __device__ __forceinline__ uint64_t nchunks() const { return (n + per - 1) / per; }
     __device__ __forceinline__ WarpChunk get(uint64_t c) const {
         const uint64_t base = c * per;
         const uint64_t rem = n - base;
-        return {ta, keys, status, base, (int)(rem < per ? rem : per)};
+        return {ta, keys, status, slots, base, (int)(rem < per ? rem : per)};
     }
 };
 
@@ -88,11 +90,14 @@ struct BatchSource {
         const BatchDesc &d = bd[lo];
         const uint64_t base = (c - prefix[lo]) * per;
         const uint64_t rem = d.n - base;
-        return {&d.ta, d.keys, d.status, base, (int)(rem < per ? rem : per)};
+        return {&d.ta, d.keys, d.status, nullptr, base, (int)(rem < per ? rem : per)};
     }
 };
 
-template <int T, int FPW0, int I, bool LOOKUP, class Src>
+// SLOTS: also write each FOUND / PUT key's slot index to the chunk's slots
+// array (the key-value extension); a separate instantiation, so that plain
+// runs pay nothing for it
+template <int T, int FPW0, int I, bool LOOKUP, class Src, bool SLOTS = false>
 __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long *ctr) {
     constexpr int W = kWordsPerBucket / T;
     constexpr uint32_t TM = (T == 32) ? 0xffffffffu : ((1u << T) - 1u);
@@ -125,8 +130,12 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
         bool pending[I], lvl2[I];
         uint8_t st[I];
         int it[I];
+        uint64_t slot_of[I];  // slot of a FOUND / PUT key (slot outputs only)
+        constexpr bool want_slots = SLOTS;
+        const uint64_t B0 = (uint64_t)kWordsPerBucket * FPW0;
 #pragma unroll
         for (int i = 0; i < I; ++i) {
+            slot_of[i] = ~0ull;
             const int pos = i * 32 + lane;
             const bool has = pos < ch.count;
             k[i] = has ? load_key(ch.keys, ta.key_bytes, ch.base + pos) : 0;
@@ -171,7 +180,7 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                 more = false;
                 // claims of all I items are issued before any outcome is read
                 uint64_t old[I], expd[I];
-                int fei[I], cli[I];
+                int fei[I], cli[I], y1[I];
                 uint32_t bmv = 0, bev = 0;
 #pragma unroll
                 for (int i = 0; i < I; ++i) {
@@ -182,11 +191,18 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                         probe_chunk<W, FPW0>(v[i], e[i], m, le);
                         const uint32_t bm = __ballot_sync(0xffffffffu, live && m) & tmask;
                         const uint32_t be = __ballot_sync(0xffffffffu, live && le) & last_lane;
+                        int y = 0;  // the matching slot's position in the bucket
+                        if (want_slots) {
+                            const int lm = bm ? __ffs(bm) - 1 - tbase : 0;
+                            y = lm * W * FPW0 +
+                                tile_shfl<T>(match_field<W, FPW0>(v[i], e[i]), lm);
+                        }
                         if (tl == r[i]) {
                             n_probe++;
                             if (bm) {
                                 st[i] = ST_FOUND;
                                 pending[i] = false;
+                                slot_of[i] = (uint64_t)a0[i] * B0 + (uint64_t)y;
                             } else if (be) {
                                 pending[i] = false;  // NOT_FOUND
                             } else {
@@ -201,6 +217,13 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                         const uint32_t be = __ballot_sync(0xffffffffu, live && fe >= 0) & tmask;
                         cli[i] = be ? __ffs(be) - 1 - tbase : 0;
                         fei[i] = fe;
+                        y1[i] = 0;
+                        if (want_slots) {
+                            // the slot that answers: the match, else the one claimed
+                            const int src = bm ? __ffs(bm) - 1 - tbase : cli[i];
+                            const int val = bm ? match_field<W, FPW0>(v[i], e[i]) : fe;
+                            y1[i] = src * W * FPW0 + tile_shfl<T>(val, src);
+                        }
                         bmv |= (bm ? 1u : 0u) << i;
                         bev |= (be ? 1u : 0u) << i;
                         old[i] = expd[i] = 0;
@@ -226,18 +249,22 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                         outcome = tile_shfl<T>(outcome, cli[i]);
                         if (tl == r[i]) {
                             n_probe++;
+                            const uint64_t at = (uint64_t)a0[i] * B0 + (uint64_t)y1[i];
                             if (bm) {
                                 st[i] = ST_FOUND;
                                 pending[i] = false;
+                                slot_of[i] = at;
                             } else if (!be) {
                                 lvl2[i] = true;  // level 1 is full for good
                             } else if (outcome == 1) {
                                 st[i] = ST_PUT;
                                 pending[i] = false;
                                 n_write++;
+                                slot_of[i] = at;
                             } else if (outcome == 2) {
                                 st[i] = ST_FOUND;  // another thread put k first
                                 pending[i] = false;
+                                slot_of[i] = at;
                             } else if (++it[i] > max_iter) {
                                 st[i] = ST_ERROR;
                                 pending[i] = false;
@@ -291,10 +318,28 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                     scan_chunk_rt<W>(va, ya, FPW1, ma, fa);
                     scan_chunk_rt<W>(vb, yb, FPW1, mb, fb);
                     const uint32_t bfound = __ballot_sync(0xffffffffu, live && (ma || mb)) & tmask;
+                    // slot outputs: where the match sits (bucket b?, lane, field)
+                    int mval = 0;
+                    bool mb_side = false;
+                    if (want_slots) {
+                        const uint32_t bma = __ballot_sync(0xffffffffu, live && ma) & tmask;
+                        mb_side = !bma;
+                        mval = ma ? match_field_rt<W>(va, ya, FPW1) : match_field_rt<W>(vb, yb, FPW1);
+                    }
+                    const uint64_t lvl2_base = L0.nb * B0;
                     if constexpr (LOOKUP) {
+                        int y = 0;
+                        if (want_slots) {
+                            const int lm = bfound ? __ffs(bfound) - 1 - tbase : 0;
+                            y = lm * LF1 + tile_shfl<T>(mval, lm);
+                        }
                         if (tl == r) {
                             n_probe += 2;
-                            if (bfound) st[i] = ST_FOUND;
+                            if (bfound) {
+                                st[i] = ST_FOUND;
+                                slot_of[i] = lvl2_base + (uint64_t)(mb_side ? ab[i] : aa[i]) * B1 +
+                                        (uint64_t)y;
+                            }
                             pending[i] = false;
                         }
                     } else {
@@ -324,11 +369,21 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                         }
                         claimed = tile_shfl<T>(claimed, cl);
                         seen = tile_shfl<T>(seen, cl);
+                        int y = 0;
+                        if (want_slots) {
+                            // the slot that answers: the match, else the one claimed
+                            const int src = bfound ? __ffs(bfound) - 1 - tbase : cl;
+                            y = src * LF1 + tile_shfl<T>(bfound ? mval : (pick_a ? fa : fb), src);
+                        }
+                        const bool in_b = bfound ? mb_side : !pick_a;
+                        const uint64_t at =
+                            lvl2_base + (uint64_t)(in_b ? ab[i] : aa[i]) * B1 + (uint64_t)y;
                         if (tl == r) {
                             n_probe += 2;
                             if (bfound) {
                                 st[i] = ST_FOUND;
                                 pending[i] = false;
+                                slot_of[i] = at;
                             } else if (load2 >= B1) {
                                 st[i] = ST_FULL;
                                 pending[i] = false;
@@ -336,9 +391,11 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                                 st[i] = ST_PUT;
                                 pending[i] = false;
                                 n_write++;
+                                slot_of[i] = at;
                             } else if (seen == (pick_a ? ya : yb)) {
                                 st[i] = ST_FOUND;
                                 pending[i] = false;
+                                slot_of[i] = at;
                             } else if (++it[i] > max_iter) {
                                 st[i] = ST_ERROR;
                                 pending[i] = false;
@@ -355,7 +412,10 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
 #pragma unroll
         for (int i = 0; i < I; ++i) {
             const int pos = i * 32 + lane;
-            if (pos < ch.count) ch.status[ch.base + pos] = st[i];
+            if (pos < ch.count) {
+                ch.status[ch.base + pos] = st[i];
+                if (want_slots) ch.slots[ch.base + pos] = slot_of[i];
+            }
             n_ops += pos < ch.count ? 1 : 0;
         }
     }
@@ -367,12 +427,12 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
     }
 }
 
-template <int T, int FPW0, int I, bool LOOKUP>
+template <int T, int FPW0, int I, bool LOOKUP, bool SLOTS = false>
 __global__ void __launch_bounds__(256)
     k_iceberg_warp(TableArgs ta, const void *__restrict__ keys, uint64_t n,
-                   uint8_t *__restrict__ status) {
-    SingleSource src{&ta, keys, status, n, (uint64_t)32 * I};
-    iceberg_warp<T, FPW0, I, LOOKUP>(src, ta.ctr);
+                   uint8_t *__restrict__ status, uint64_t *__restrict__ slots) {
+    SingleSource src{&ta, keys, status, slots, n, (uint64_t)32 * I};
+    iceberg_warp<T, FPW0, I, LOOKUP, SingleSource, SLOTS>(src, ta.ctr);
 }
 
 // one persistent launch over many tables; shared memory holds the prefix of

@@ -1,5 +1,6 @@
 // Instantiations and launcher of the warp-batched iceberg engine for one
-// table (find-or-put and lookup).
+// table (find-or-put and lookup); runs that return slot indices go to the
+// instantiations in iceberg_slots.cu.
 #include "cht_kernels.cuh"
 #include "cht_launch.h"
 #include "cht_warp.cuh"
@@ -9,51 +10,52 @@ namespace cht {
 // ---- warp engine, one table ----------------------------------------------
 template <int T, int FPW0, int I, bool LOOKUP>
 static cudaError_t run_warp(const LaunchParams &lp, const TableArgs &ta, const void *keys,
-                            uint64_t n, uint8_t *status) {
+                            uint64_t n, uint8_t *status, uint64_t *slots) {
     auto kern = k_iceberg_warp<T, FPW0, I, LOOKUP>;
     const int blocks = grid_blocks_warp((const void *)kern, lp, (n + I - 1) / I);
-    kern<<<blocks, lp.cta, 0, lp.stream>>>(ta, keys, n, status);
+    kern<<<blocks, lp.cta, 0, lp.stream>>>(ta, keys, n, status, slots);
     return cudaGetLastError();
 }
 
 template <int T, int FPW0, bool LOOKUP>
 static cudaError_t by_items(const LaunchParams &lp, const TableArgs &ta, const void *keys,
-                            uint64_t n, uint8_t *status) {
+                            uint64_t n, uint8_t *status, uint64_t *slots) {
     switch (batch_items(lp.items)) {
-        case 1: return run_warp<T, FPW0, 1, LOOKUP>(lp, ta, keys, n, status);
-        case 2: return run_warp<T, FPW0, 2, LOOKUP>(lp, ta, keys, n, status);
-        default: return run_warp<T, FPW0, 4, LOOKUP>(lp, ta, keys, n, status);
+        case 1: return run_warp<T, FPW0, 1, LOOKUP>(lp, ta, keys, n, status, slots);
+        case 2: return run_warp<T, FPW0, 2, LOOKUP>(lp, ta, keys, n, status, slots);
+        default: return run_warp<T, FPW0, 4, LOOKUP>(lp, ta, keys, n, status, slots);
     }
 }
 
 template <int T, bool LOOKUP>
 static cudaError_t by_fpw(int fpw0, const LaunchParams &lp, const TableArgs &ta,
-                          const void *keys, uint64_t n, uint8_t *status) {
+                          const void *keys, uint64_t n, uint8_t *status, uint64_t *slots) {
     switch (fpw0) {
-        case 1: return by_items<T, 1, LOOKUP>(lp, ta, keys, n, status);
-        case 2: return by_items<T, 2, LOOKUP>(lp, ta, keys, n, status);
-        case 3: return by_items<T, 3, LOOKUP>(lp, ta, keys, n, status);
-        case 4: return by_items<T, 4, LOOKUP>(lp, ta, keys, n, status);
+        case 1: return by_items<T, 1, LOOKUP>(lp, ta, keys, n, status, slots);
+        case 2: return by_items<T, 2, LOOKUP>(lp, ta, keys, n, status, slots);
+        case 3: return by_items<T, 3, LOOKUP>(lp, ta, keys, n, status, slots);
+        case 4: return by_items<T, 4, LOOKUP>(lp, ta, keys, n, status, slots);
     }
     return cudaErrorInvalidValue;
 }
 
 template <bool LOOKUP>
 static cudaError_t by_tile(int T, int fpw0, const LaunchParams &lp, const TableArgs &ta,
-                           const void *keys, uint64_t n, uint8_t *status) {
+                           const void *keys, uint64_t n, uint8_t *status, uint64_t *slots) {
     switch (T) {
-        case 4: return by_fpw<4, LOOKUP>(fpw0, lp, ta, keys, n, status);
-        case 8: return by_fpw<8, LOOKUP>(fpw0, lp, ta, keys, n, status);
-        case 16: return by_fpw<16, LOOKUP>(fpw0, lp, ta, keys, n, status);
+        case 4: return by_fpw<4, LOOKUP>(fpw0, lp, ta, keys, n, status, slots);
+        case 8: return by_fpw<8, LOOKUP>(fpw0, lp, ta, keys, n, status, slots);
+        case 16: return by_fpw<16, LOOKUP>(fpw0, lp, ta, keys, n, status, slots);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_iceberg_warp(int T, int fpw0, bool lookup, const LaunchParams &lp,
                                 const TableArgs &ta, const void *keys, uint64_t n,
-                                uint8_t *status) {
-    return lookup ? by_tile<true>(T, fpw0, lp, ta, keys, n, status)
-                  : by_tile<false>(T, fpw0, lp, ta, keys, n, status);
+                                uint8_t *status, uint64_t *slots) {
+    if (slots) return launch_iceberg_warp_slots(T, fpw0, lookup, lp, ta, keys, n, status, slots);
+    return lookup ? by_tile<true>(T, fpw0, lp, ta, keys, n, status, slots)
+                  : by_tile<false>(T, fpw0, lp, ta, keys, n, status, slots);
 }
 
 }  // namespace cht

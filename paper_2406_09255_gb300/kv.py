@@ -1,0 +1,48 @@
+"""Key-value map over an iceberg table: values live in a device array indexed
+by the stable slot of their key (iceberg entries never move once placed), so
+a put is a find-or-put that returns slots plus a scatter of the values, and a
+get is a lookup that returns slots plus a gather. Both moves are library
+kernels (cht_values_scatter / cht_values_gather)."""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+from .table import Table, _stream_handle
+
+_VALUE_BYTES = {torch.int32: 4, torch.float32: 4, torch.int64: 8, torch.float64: 8}
+
+
+class KVMap:
+    def __init__(self, table: Table, value_dtype=torch.int64):
+        if table.cfg.kind != 1:
+            raise ValueError("a key-value map needs an iceberg table (stable slots)")
+        if value_dtype not in _VALUE_BYTES:
+            raise ValueError(f"value dtype must be one of {list(_VALUE_BYTES)}")
+        self.table = table
+        self.value_bytes = _VALUE_BYTES[value_dtype]
+        self.values = torch.zeros(table.slots, dtype=value_dtype, device=table.device)
+        self._L = _lib.load()
+
+    def put(self, keys: torch.Tensor, values: torch.Tensor, stream=None):
+        """Insert or assign. Returns (status, slots). A key given twice in one
+        call keeps one of its values, which one is unspecified. FULL keys
+        store nothing."""
+        if values.dtype != self.values.dtype or values.numel() != keys.numel():
+            raise ValueError("one value of the map's dtype per key")
+        values = values.contiguous()
+        status, slots = self.table.find_or_put(keys, stream=stream, slots=True)
+        _lib.check(self._L.cht_values_scatter(slots.data_ptr(), keys.numel(), values.data_ptr(),
+                                              self.value_bytes, self.values.data_ptr(),
+                                              self.values.numel(), _stream_handle(stream)))
+        return status, slots
+
+    def get(self, keys: torch.Tensor, stream=None):
+        """Returns (values, status): zero values for keys not found."""
+        status, slots = self.table.find(keys, stream=stream, slots=True)
+        out = torch.empty(keys.numel(), dtype=self.values.dtype, device=self.table.device)
+        _lib.check(self._L.cht_values_gather(slots.data_ptr(), keys.numel(),
+                                             self.values.data_ptr(), self.value_bytes,
+                                             self.values.numel(), out.data_ptr(),
+                                             _stream_handle(stream)))
+        return out, status

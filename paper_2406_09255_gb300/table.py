@@ -135,17 +135,40 @@ class Table:
                                  _stream_handle(stream)))
         return status
 
-    def find(self, keys: torch.Tensor, status=None, stream=None):
-        keys, status = self._prep(keys, status)
-        check(self._L.cht_find(self._h, keys.data_ptr(), keys.numel(), status.data_ptr(),
-                               _stream_handle(stream)))
-        return status
+    def _slots(self, n: int, slots):
+        if slots is None or slots is True:
+            return torch.empty(n, dtype=torch.int64, device=self.device)
+        if slots.dtype != torch.int64 or slots.device != self.device or slots.numel() < n:
+            raise ValueError("slots must be an int64 tensor on the table's device")
+        return slots
 
-    def find_or_put(self, keys: torch.Tensor, status=None, stream=None):
+    def find(self, keys: torch.Tensor, status=None, stream=None, slots=None):
+        """Lookups. With slots (True, or an int64 tensor to fill) on an iceberg
+        table, also returns each found key's slot (-1 when not found)."""
         keys, status = self._prep(keys, status)
-        check(self._L.cht_find_or_put(self._h, keys.data_ptr(), keys.numel(), status.data_ptr(),
-                                      _stream_handle(stream)))
-        return status
+        if slots is None or slots is False:
+            check(self._L.cht_find(self._h, keys.data_ptr(), keys.numel(), status.data_ptr(),
+                                   _stream_handle(stream)))
+            return status
+        slots = self._slots(keys.numel(), slots)
+        check(self._L.cht_find_slots(self._h, keys.data_ptr(), keys.numel(), status.data_ptr(),
+                                     slots.data_ptr(), _stream_handle(stream)))
+        return status, slots
+
+    def find_or_put(self, keys: torch.Tensor, status=None, stream=None, slots=None):
+        """Find-or-put (iceberg). With slots (True, or an int64 tensor to fill),
+        also returns the slot of each FOUND / PUT key (-1 otherwise): a handle
+        that stays valid until clear()."""
+        keys, status = self._prep(keys, status)
+        if slots is None or slots is False:
+            check(self._L.cht_find_or_put(self._h, keys.data_ptr(), keys.numel(),
+                                          status.data_ptr(), _stream_handle(stream)))
+            return status
+        slots = self._slots(keys.numel(), slots)
+        check(self._L.cht_find_or_put_slots(self._h, keys.data_ptr(), keys.numel(),
+                                            status.data_ptr(), slots.data_ptr(),
+                                            _stream_handle(stream)))
+        return status, slots
 
     def enumerate(self, cap: int | None = None, out=None, count=None, stream=None):
         """All stored keys (unspecified order), trimmed to the stored count."""

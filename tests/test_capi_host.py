@@ -121,3 +121,14 @@ def test_random_read_rejects_bad_arguments_without_a_launch(lib):
     assert "power of two" in L.cht_last_error().decode()
     assert L.cht_random_read(ctypes.c_void_p((1 << 20) + 8), 1 << 20, 128, 10, 0, sink,
                              None) == lib.CHT_ERR_INVALID
+
+
+def test_value_moves_reject_bad_arguments_without_a_launch(lib):
+    L = lib.load()
+    fake = ctypes.c_void_p(1 << 20)
+    assert L.cht_values_scatter(fake, 10, fake, 3, fake, 100, None) == lib.CHT_ERR_INVALID
+    assert "value_bytes" in L.cht_last_error().decode()
+    assert L.cht_values_gather(fake, 10, fake, 8, 100, None, None) == lib.CHT_ERR_INVALID
+    assert L.cht_values_gather(ctypes.c_void_p((1 << 20) + 4), 10, fake, 8, 100, fake,
+                               None) == lib.CHT_ERR_INVALID
+    assert L.cht_values_scatter(fake, 0, fake, 8, fake, 100, None) == lib.CHT_OK  # empty: nothing to do
