@@ -650,6 +650,69 @@ def run_iceberg_variants(args, dev):
     print(json.dumps(out))
 
 
+def run_kv(args, dev):
+    """Key-value extension on the 2^22 + 2^19 compact iceberg table (48-bit
+    keys, 8-byte values): put = find-or-put with slots + value scatter, get =
+    lookup with slots + value gather, against plain find-or-put and lookups
+    on the same keys. Puts of unique keys fill the table to 0.8 in 2^24-key
+    batches; gets are 2^26 queries at 50 % hit."""
+    from paper_2406_09255_gb300 import ICEBERG, KVMap, Table
+    from paper_2406_09255_gb300 import workloads as W
+    seed = W.SEED_BASE + 7
+    nq = 1 << 26
+
+    def ev_ms(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    res = {}
+    for mode in ("plain", "kv"):
+        t = Table(ICEBERG, 48, 1 << 22, 1 << 19, seed=7000, device=dev)
+        n = int(0.8 * t.slots)
+        keys = W.unique_keys(0, n, 48, seed, device=dev)
+        vals = torch.arange(n, dtype=torch.int64, device=dev)
+        kv = KVMap(t, torch.int64) if mode == "kv" else None
+        put_ms, get_ms = [], []
+        for rep in range(max(2, args.steps)):
+            t.clear()
+            torch.cuda.synchronize()
+            ms = 0.0
+            for lo in range(0, n, 1 << 24):
+                hi = min(n, lo + (1 << 24))
+                if kv is None:
+                    ms += ev_ms(lambda: t.find_or_put(keys[lo:hi]))
+                else:
+                    ms += ev_ms(lambda: kv.put(keys[lo:hi], vals[lo:hi]))
+            put_ms.append(ms)
+            q, present = W.find_queries(n, nq, 0.5, 48, seed, n, device=dev,
+                                        shuffle_seed=seed + rep)
+            if kv is None:
+                get_ms.append(ev_ms(lambda: t.find(q)))
+            else:
+                out = {}
+                get_ms.append(ev_ms(lambda: out.setdefault("r", kv.get(q))))
+                got, st = out["r"]
+                # present keys read back their own values (value = key index)
+                assert bool((st == 1).eq(present).all())
+            del q, present
+        res[mode] = {"put_mops": n / statistics.median(put_ms) / 1e3,
+                     "get_mops": nq / statistics.median(get_ms) / 1e3}
+        del t, keys, vals, kv
+        torch.cuda.empty_cache()
+    out = {"metric": "Mops/s key-value put / get vs plain find-or-put / find", "unit": "Mops/s",
+           "value": res["kv"]["get_mops"], "n_gpus": 1, "higher_is_better": True,
+           "dtype": "u64", "data": "synthetic",
+           "config": {"workload": "kv: compact iceberg 2^22 + 2^19 buckets, 48-bit keys, "
+                                  "8-byte values, put to fill 0.8 in 2^24-key batches, 2^26 "
+                                  "gets at 50% hit"},
+           "results": res}
+    print(json.dumps(out))
+
+
 def run_served(args, dev):
     """16 resident compact iceberg tables (48-bit keys, 2^20..2^23 primary
     buckets), Poisson request arrivals at rates relative to the saturated
@@ -766,7 +829,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     others = {"iceberg_stream": run_iceberg_stream, "batch256": run_batch256,
               "served": run_served, "iceberg_variants": run_iceberg_variants,
-              "random_read": run_random_read}
+              "random_read": run_random_read, "kv": run_kv}
     ap.add_argument("--workload", default="cuckoo_2e24", choices=sorted(WORKLOADS) + sorted(others))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
