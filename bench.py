@@ -156,8 +156,9 @@ def dist_setup():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        dist.init_process_group(backend)
+        if not dist.is_initialized():
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -165,6 +166,12 @@ def barrier(ws):
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def job_rate_mops(ops_per_step_per_rank: int, steps: int, ws: int, ms_max: float) -> float:
+    """Whole-job throughput: the operations every rank did (each replica runs
+    the full step) over the slowest rank's time."""
+    return ops_per_step_per_rank * steps * ws / (ms_max * 1e-3) / 1e6
 
 
 def max_over_ranks(ws, x: float, device) -> float:
@@ -942,10 +949,9 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec)
 
-    total_ops = wl.ops_per_step * args.steps * ws
     out = {
         "metric": METRIC,
-        "value": total_ops / (ms_max * 1e-3) / 1e6,
+        "value": job_rate_mops(wl.ops_per_step, args.steps, ws, ms_max),
         "unit": "Mops/s",
         "n_gpus": ws,
         "steps": args.steps,
