@@ -75,9 +75,10 @@ typedef struct cht_table cht_table; /* opaque host handle */
  *                       0: store whole keys, one 64-bit slot each.
  * key_bits              w, 2..62 (at most 32 when key_bytes = 4).
  * key_bytes             width of the caller's key arrays: 4 or 8.
- * num_buckets           buckets of the cuckoo table / iceberg primary level.
- *                       A power of two when compact = 1 (Section 4.5).
- * num_buckets_backyard  iceberg secondary-level buckets (ignored for cuckoo).
+ * num_buckets           buckets of the cuckoo table / iceberg primary level,
+ *                       1..2^32. A power of two when compact = 1 (Section 4.5).
+ * num_buckets_backyard  iceberg secondary-level buckets (ignored for cuckoo),
+ *                       1..2^32.
  * fields_per_word       slots per 64-bit word of level 0, 1..4 (slot width
  *                       64/fields_per_word bits); 0 = the densest packing in
  *                       which every entry fits. Whole-key tables use 1.

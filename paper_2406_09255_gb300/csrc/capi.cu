@@ -64,6 +64,8 @@ int tag_bits(int kind, int level) { return (kind == CHT_ICEBERG && level == 0) ?
 int resolve_level(cht_config &c, int level, uint64_t nb, int32_t &fpw) {
     const char *lname = level ? "num_buckets_backyard" : "num_buckets";
     if (nb < 1) return fail(CHT_ERR_INVALID, "%s must be >= 1", lname);
+    // the kernels carry bucket indices in 32 bits (2^32 buckets = 512 GiB)
+    if (nb > (1ull << 32)) return fail(CHT_ERR_INVALID, "%s must be at most 2^32", lname);
     if (c.compact && !is_pow2(nb))
         return fail(CHT_ERR_INVALID, "%s = %llu must be a power of two for a compact table",
                     lname, (unsigned long long)nb);

@@ -97,6 +97,7 @@ def test_bit_budget_section_5_1(lib):
     (dict(kind=1, key_bits=32, num_buckets=16, num_buckets_backyard=0), "backyard"),
     (dict(kind=0, key_bits=62, num_buckets=4, fields_per_word=2), "bits"),
     (dict(kind=0, key_bits=32, num_buckets=16, lookups_in_flight=2), "lookups_in_flight"),
+    (dict(kind=0, key_bits=60, num_buckets=1 << 33), "at most 2^32"),
     (dict(kind=0, key_bits=32, num_buckets=16, lookups_in_flight=16), "lookups_in_flight"),
 ])
 def test_invalid_configs_rejected_with_message(lib, kw, frag):
