@@ -913,6 +913,10 @@ def main():
         p, wr, cf, ops = counts[("insert", fi)]
         entry = {"fill": f, "insert_mops": n_ins / ims / 1e3,
                  "insert_probes_per_op": p / max(ops, 1),
+                 "insert_writes_per_op": wr / max(ops, 1),
+                 # a put reads its line and later writes back the dirtied sector:
+                 # two random DRAM accesses per probe-and-write
+                 "insert_random_accesses_per_s": (p + wr) / (ims * 1e-3),
                  "failed_inserts": counts[("insert_failed", fi)]}
         for hi, h in enumerate(spec["hits"]):
             fms_i = statistics.median(ph[("find", fi, hi)])
@@ -930,6 +934,8 @@ def main():
     achieved = fb / (fms * 1e-3) / 1e9
     ceiling = random_read_ceiling(dev)
     probe_rate = fprobes / (fms * 1e-3)
+    for entry in phases:
+        entry["insert_frac_of_random_ceiling"] = entry["insert_random_accesses_per_s"] / ceiling
     launches = len([1 for k in ph if k[0] == "find"])
     tpu = traffic_per_unit("cuckoo_find")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -252,6 +252,26 @@ int cht_values_gather(const uint64_t *d_slots, size_t n, const void *d_store, in
                       uint64_t store_slots, void *d_out, void *stream);
 
 /*
+ * Fused key-value put and get: one kernel each, the value move done by the
+ * lane that answers the key. cht_kv_put = cht_find_or_put, then for every
+ * FOUND or PUT key i d_store[slot(i)] = d_values[i] (insert or assign; a key
+ * given twice in one call keeps one of its values, which one is unspecified;
+ * FULL keys store nothing). cht_kv_get = cht_find, then d_out[i] =
+ * d_store[slot(i)] for FOUND keys and zero otherwise. d_store holds
+ * store_slots values of value_bytes (4, 8 or 16) and must cover the table's
+ * slots (nb0 * B0 + nb1 * B1, see above) for every key to have its value;
+ * slots at or past store_slots are skipped. Iceberg tables only
+ * (CHT_ERR_UNSUPPORTED otherwise); values aligned to value_bytes
+ * (CHT_ERR_INVALID otherwise); keys, statuses and errors as for
+ * cht_find_or_put / cht_find.
+ */
+int cht_kv_put(cht_table *t, const void *d_keys, size_t n, const void *d_values, int value_bytes,
+               void *d_store, uint64_t store_slots, uint8_t *d_status, void *stream);
+int cht_kv_get(const cht_table *t, const void *d_keys, size_t n, const void *d_store,
+               int value_bytes, uint64_t store_slots, void *d_out, uint8_t *d_status,
+               void *stream);
+
+/*
  * Write every stored key, decoded as k = pi_j^-1(a . r) (Section 2.4), to
  * d_out (key_bytes each) in unspecified order, at most cap keys. *d_count (a
  * device uint64) receives the number of stored keys, which may exceed cap;

@@ -90,6 +90,10 @@ SIGNATURES = {
     "cht_find_slots": (ctypes.c_int, [_vp, _vp, _sz, _vp, _vp, _vp]),
     "cht_values_scatter": (ctypes.c_int, [_vp, _sz, _vp, ctypes.c_int, _vp, ctypes.c_uint64, _vp]),
     "cht_values_gather": (ctypes.c_int, [_vp, _sz, _vp, ctypes.c_int, ctypes.c_uint64, _vp, _vp]),
+    "cht_kv_put": (ctypes.c_int, [_vp, _vp, _sz, _vp, ctypes.c_int, _vp, ctypes.c_uint64, _vp,
+                                  _vp]),
+    "cht_kv_get": (ctypes.c_int, [_vp, _vp, _sz, _vp, ctypes.c_int, ctypes.c_uint64, _vp, _vp,
+                                  _vp]),
 }
 
 _lock = threading.Lock()

@@ -393,6 +393,45 @@ int cht_values_gather(const uint64_t *d_slots, size_t n, const void *d_store, in
     return values_call(false, d_slots, n, d_store, d_out, value_bytes, store_slots, stream);
 }
 
+static int kv_check(const cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
+                    const void *values, int value_bytes, const void *store) {
+    int e = check_keys(t, d_keys, n, d_status);
+    if (e) return e;
+    if (t->cfg.kind != CHT_ICEBERG)
+        return fail(CHT_ERR_UNSUPPORTED, "key-value maps need iceberg tables (stable slots)");
+    if (value_bytes != 4 && value_bytes != 8 && value_bytes != 16)
+        return fail(CHT_ERR_INVALID, "value_bytes must be 4, 8 or 16");
+    if (n && (!values || !store)) return fail(CHT_ERR_INVALID, "null value pointer");
+    if ((uintptr_t)values % value_bytes || (uintptr_t)store % value_bytes)
+        return fail(CHT_ERR_INVALID, "values not aligned to value_bytes");
+    return CHT_OK;
+}
+
+int cht_kv_put(cht_table *t, const void *d_keys, size_t n, const void *d_values, int value_bytes,
+               void *d_store, uint64_t store_slots, uint8_t *d_status, void *stream) {
+    int e = kv_check(t, d_keys, n, d_status, d_values, value_bytes, d_store);
+    if (e) return e;
+    if (n == 0) return ok();
+    const LaunchParams lp = launch_params(t, stream);
+    const KVArgs kv{d_values, nullptr, d_store, store_slots, value_bytes};
+    cudaError_t ce = launch_iceberg(tile_for(t, kOpIcebergFop), t->cfg.fields_per_word, false, lp,
+                                    t->args, d_keys, n, d_status, nullptr, &kv);
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "key-value put kernel launch");
+}
+
+int cht_kv_get(const cht_table *t, const void *d_keys, size_t n, const void *d_store,
+               int value_bytes, uint64_t store_slots, void *d_out, uint8_t *d_status,
+               void *stream) {
+    int e = kv_check(t, d_keys, n, d_status, d_out, value_bytes, d_store);
+    if (e) return e;
+    if (n == 0) return ok();
+    const LaunchParams lp = launch_params(t, stream);
+    const KVArgs kv{nullptr, d_out, const_cast<void *>(d_store), store_slots, value_bytes};
+    cudaError_t ce = launch_iceberg(tile_for(t, kOpIcebergFind), t->cfg.fields_per_word, true, lp,
+                                    t->args, d_keys, n, d_status, nullptr, &kv);
+    return ce == cudaSuccess ? ok() : cuda_fail(ce, "key-value get kernel launch");
+}
+
 int cht_find_or_put(cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
                     void *stream) {
     int e = check_keys(t, d_keys, n, d_status);

@@ -326,6 +326,62 @@ __device__ __forceinline__ void probe_chunk(const uint64_t (&v)[W], uint64_t ent
     last_empty = Fields<FPW>::get(v[W - 1], FPW - 1) == 0;
 }
 
+// probe_chunk / scan_chunk that also give the local field index of the match
+// (-1 if none) from the same zero-field masks: the first word with a flag is
+// picked with selects, then one find-first-set gives its lowest flagged field
+template <int FPW>
+__device__ __forceinline__ int first_flag_field(uint64_t zsel, int wsel) {
+    const int b = __ffsll((long long)zsel) - 1;  // -1 when zsel == 0
+    return zsel ? wsel * FPW + b / Swar<FPW>::S : -1;
+}
+template <int W, int FPW>
+__device__ __forceinline__ void probe_chunk_pos(const uint64_t (&v)[W], uint64_t entry,
+                                                bool &match, bool &last_empty, int &pos) {
+    using Z = Swar<FPW>;
+    const uint64_t pat = Z::spread(entry);
+    uint64_t zsel = 0;
+    int wsel = 0;
+#pragma unroll
+    for (int i = W - 1; i >= 0; --i) {
+        const uint64_t z = Z::zeros(v[i] ^ pat);
+        wsel = z ? i : wsel;
+        zsel = z ? z : zsel;
+    }
+    pos = first_flag_field<FPW>(zsel, wsel);
+    match = zsel != 0;
+    last_empty = Fields<FPW>::get(v[W - 1], FPW - 1) == 0;
+}
+template <int W, int FPW>
+__device__ __forceinline__ void scan_chunk_pos(const uint64_t (&v)[W], uint64_t entry, bool &match,
+                                               int &first_empty, int &pos) {
+    using Z = Swar<FPW>;
+    const uint64_t pat = Z::spread(entry);
+    int empties = 0;
+    uint64_t zsel = 0;
+    int wsel = 0;
+#pragma unroll
+    for (int i = W - 1; i >= 0; --i) {
+        const uint64_t z = Z::zeros(v[i] ^ pat);
+        wsel = z ? i : wsel;
+        zsel = z ? z : zsel;
+        empties += __popcll(Z::zeros(v[i]));
+    }
+    pos = first_flag_field<FPW>(zsel, wsel);
+    match = zsel != 0;
+    first_empty = empties ? W * FPW - empties : -1;
+}
+
+template <int W>
+__device__ __forceinline__ void scan_chunk_rt_pos(const uint64_t (&v)[W], uint64_t entry, int fpw,
+                                                  bool &match, int &first_empty, int &pos) {
+    switch (fpw) {
+        case 1: scan_chunk_pos<W, 1>(v, entry, match, first_empty, pos); break;
+        case 2: scan_chunk_pos<W, 2>(v, entry, match, first_empty, pos); break;
+        case 3: scan_chunk_pos<W, 3>(v, entry, match, first_empty, pos); break;
+        default: scan_chunk_pos<W, 4>(v, entry, match, first_empty, pos); break;
+    }
+}
+
 // local field index (word * FPW + field) of the owned field equal to entry,
 // or -1: the lowest flagged field of the first word with a flag is exact
 // (see Swar), and a table holds an entry at most once
@@ -528,6 +584,72 @@ __device__ __forceinline__ bool claim_field_rt(int fpw, uint64_t *wp, int f, uin
         case 2: return claim_field<2>(wp, f, snap_word, entry, seen, fails);
         case 3: return claim_field<3>(wp, f, snap_word, entry, seen, fails);
         default: return claim_field<4>(wp, f, snap_word, entry, seen, fails);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Values of the key-value extension: a caller array of nstore values of
+// vbytes (4, 8 or 16) indexed by slot. A put copies value i of its batch to
+// the key's slot; a get copies the slot's value to output i (zero when the
+// key has no slot).
+// ---------------------------------------------------------------------------
+struct KVArgs {
+    const void *vin;  // put: the batch's values
+    void *vout;       // get: output values
+    void *store;      // the value array (null: no value moves)
+    uint64_t nstore;  // its length in values
+    int vbytes;
+};
+
+// one value as two words (4-byte values use lo only)
+struct KVal {
+    uint64_t lo, hi;
+};
+__device__ __forceinline__ KVal kv_read(const void *base, uint64_t i, int vbytes) {
+    if (vbytes == 4) return {static_cast<const uint32_t *>(base)[i], 0};
+    if (vbytes == 8) return {static_cast<const uint64_t *>(base)[i], 0};
+    const ulonglong2 v = static_cast<const ulonglong2 *>(base)[i];
+    return {v.x, v.y};
+}
+__device__ __forceinline__ void kv_write(void *base, uint64_t i, int vbytes, KVal v) {
+    if (vbytes == 4)
+        static_cast<uint32_t *>(base)[i] = static_cast<uint32_t>(v.lo);
+    else if (vbytes == 8)
+        static_cast<uint64_t *>(base)[i] = v.lo;
+    else
+        static_cast<ulonglong2 *>(base)[i] = make_ulonglong2(v.lo, v.hi);
+}
+
+__device__ __forceinline__ void kv_move(const KVArgs &kv, bool put, uint64_t i, uint64_t slot) {
+    const bool has = slot < kv.nstore;
+    switch (kv.vbytes) {
+        case 4: {
+            uint32_t *st = static_cast<uint32_t *>(kv.store);
+            if (put) {
+                if (has) st[slot] = static_cast<const uint32_t *>(kv.vin)[i];
+            } else {
+                static_cast<uint32_t *>(kv.vout)[i] = has ? st[slot] : 0u;
+            }
+            break;
+        }
+        case 8: {
+            uint64_t *st = static_cast<uint64_t *>(kv.store);
+            if (put) {
+                if (has) st[slot] = static_cast<const uint64_t *>(kv.vin)[i];
+            } else {
+                static_cast<uint64_t *>(kv.vout)[i] = has ? st[slot] : 0ull;
+            }
+            break;
+        }
+        default: {
+            ulonglong2 *st = static_cast<ulonglong2 *>(kv.store);
+            if (put) {
+                if (has) st[slot] = static_cast<const ulonglong2 *>(kv.vin)[i];
+            } else {
+                static_cast<ulonglong2 *>(kv.vout)[i] = has ? st[slot] : make_ulonglong2(0, 0);
+            }
+            break;
+        }
     }
 }
 

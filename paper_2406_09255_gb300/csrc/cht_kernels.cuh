@@ -401,6 +401,7 @@ struct SingleWork : TileWork<T> {
     uint64_t n;
     uint8_t *status;
     uint64_t *slots;  // optional slot index per key (iceberg key-value handle)
+    const KVArgs *kv;  // optional value moves (key-value extension)
     __device__ __forceinline__ const TableArgs &ta() const { return *tap; }
     __device__ __forceinline__ void next() { this->refill(keys, tap->key_bytes, n, status); }
 };
@@ -471,7 +472,8 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
         // its local field, and whether it is in secondary bucket b
         int mlane = 0, mloc = -1;
         bool min_b = false;
-        if (tw.slots) {
+        const bool want_slots = tw.slots || tw.kv->store;
+        if (want_slots) {
             const uint32_t bma = tile_ballot<T>(p2 && ma);
             const int ml = p1 ? match_field<W, FPW0>(v0, e0)
                               : (ma ? match_field_rt<W>(va, ea, FPW1) : match_field_rt<W>(vb, eb, FPW1));
@@ -518,7 +520,7 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
         claimed = tile_shfl<T>(claimed, cl);
         seen = tile_shfl<T>(seen, cl);
         int cloc = 0;  // the claimed slot's local field in lane cl (slot outputs only)
-        if (tw.slots) cloc = tile_shfl<T>(lvl == 1 ? f0 : (pick_a ? fa : fb), cl);
+        if (want_slots) cloc = tile_shfl<T>(lvl == 1 ? f0 : (pick_a ? fa : fb), cl);
 
         if (act) {
             bool fin = true;
@@ -559,7 +561,7 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
                     tw.s_st[tw.q] = st;
                     if (st == ST_ERROR) atomicOr(ta.err, 1u);
                     n_ops++;
-                    if (tw.slots) {
+                    if (want_slots) {
                         // FOUND by a match: the matching slot; PUT, or FOUND
                         // after losing the claim to k itself: the claimed slot
                         const uint64_t B0 = (uint64_t)kWordsPerBucket * FPW0;
@@ -576,7 +578,8 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
                                        (uint64_t)(ln * LF1 + loc);
                             }
                         }
-                        tw.slots[tw.base + tw.q] = slot;
+                        if (tw.slots) tw.slots[tw.base + tw.q] = slot;
+                        if (tw.kv->store) kv_move(*tw.kv, !LOOKUP, tw.base + tw.q, slot);
                     }
                 }
                 tw.q++;
@@ -597,7 +600,7 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
 template <int T, int FPW0, bool LOOKUP>
 __global__ void __launch_bounds__(256)
     k_iceberg(TableArgs ta, const void *__restrict__ keys, uint64_t n,
-              uint8_t *__restrict__ status, uint64_t *__restrict__ slots, int items) {
+              uint8_t *__restrict__ status, uint64_t *__restrict__ slots, KVArgs kv, int items) {
     extern __shared__ uint64_t smem[];
     SingleWork<T> tw;
     tw.init(smem, reinterpret_cast<uint8_t *>(smem + (size_t)blockDim.x * items), items, n,
@@ -607,6 +610,7 @@ __global__ void __launch_bounds__(256)
     tw.n = n;
     tw.status = status;
     tw.slots = slots;
+    tw.kv = &kv;
     iceberg_engine<T, FPW0, LOOKUP>(tw, ta.ctr);
 }
 

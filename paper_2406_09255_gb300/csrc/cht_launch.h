@@ -77,17 +77,19 @@ cudaError_t launch_cuckoo_insert(int T, int fpw, const LaunchParams &lp, const T
                                  uint64_t *dropped);
 cudaError_t launch_cuckoo_find(int T, int fpw, const LaunchParams &lp, const TableArgs &ta,
                                const void *keys, uint64_t n, uint8_t *status);
-// slots (nullable): per-key slot index output of iceberg operations
+// slots (nullable): per-key slot index output of iceberg operations; kv
+// (nullable): value moves of the key-value extension
 cudaError_t launch_iceberg(int T, int fpw0, bool lookup, const LaunchParams &lp,
                            const TableArgs &ta, const void *keys, uint64_t n, uint8_t *status,
-                           uint64_t *slots = nullptr);
+                           uint64_t *slots = nullptr, const KVArgs *kv = nullptr);
 cudaError_t launch_iceberg_warp(int T, int fpw0, bool lookup, const LaunchParams &lp,
                                 const TableArgs &ta, const void *keys, uint64_t n,
-                                uint8_t *status, uint64_t *slots = nullptr);
-// the warp-batched engine with slot outputs (one key per lane)
+                                uint8_t *status, uint64_t *slots = nullptr,
+                                const KVArgs *kv = nullptr);
+// the warp-batched engine with slot outputs and value moves (one key per lane)
 cudaError_t launch_iceberg_warp_slots(int T, int fpw0, bool lookup, const LaunchParams &lp,
                                       const TableArgs &ta, const void *keys, uint64_t n,
-                                      uint8_t *status, uint64_t *slots);
+                                      uint8_t *status, uint64_t *slots, const KVArgs &kv);
 
 struct BatchDesc;
 // launch shape of the allocation-free fused find-or-put

@@ -51,6 +51,7 @@ struct WarpChunk {
     const void *keys;
     uint8_t *status;
     uint64_t *slots;  // optional slot index per key (iceberg key-value handle)
+    const KVArgs *kv;  // optional value moves (key-value extension)
     uint64_t base;
     int count;
 };
@@ -61,13 +62,14 @@ struct SingleSource {
     const void *keys;
     uint8_t *status;
     uint64_t *slots;
+    const KVArgs *kv;
     uint64_t n;
     uint64_t per;  // keys per chunk
     __device__ __forceinline__ uint64_t nchunks() const { return (n + per - 1) / per; }
     __device__ __forceinline__ WarpChunk get(uint64_t c) const {
         const uint64_t base = c * per;
         const uint64_t rem = n - base;
-        return {ta, keys, status, slots, base, (int)(rem < per ? rem : per)};
+        return {ta, keys, status, slots, kv, base, (int)(rem < per ? rem : per)};
     }
 };
 
@@ -90,7 +92,7 @@ struct BatchSource {
         const BatchDesc &d = bd[lo];
         const uint64_t base = (c - prefix[lo]) * per;
         const uint64_t rem = d.n - base;
-        return {&d.ta, d.keys, d.status, nullptr, base, (int)(rem < per ? rem : per)};
+        return {&d.ta, d.keys, d.status, nullptr, nullptr, base, (int)(rem < per ? rem : per)};
     }
 };
 
@@ -131,14 +133,20 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
         uint8_t st[I];
         int it[I];
         uint64_t slot_of[I];  // slot of a FOUND / PUT key (slot outputs only)
+        // value moves: a put's value is read with the key, a get's value as
+        // soon as the key is found, so both loads overlap the probe passes
+        KVal vpre[I];
+        const bool moves = SLOTS && ch.kv->store != nullptr;
         constexpr bool want_slots = SLOTS;
         const uint64_t B0 = (uint64_t)kWordsPerBucket * FPW0;
 #pragma unroll
         for (int i = 0; i < I; ++i) {
             slot_of[i] = ~0ull;
+            vpre[i] = KVal{0, 0};
             const int pos = i * 32 + lane;
             const bool has = pos < ch.count;
             k[i] = has ? load_key(ch.keys, ta.key_bytes, ch.base + pos) : 0;
+            if (!LOOKUP && moves && has) vpre[i] = kv_read(ch.kv->vin, ch.base + pos, ch.kv->vbytes);
             pending[i] = has && valid_key(k[i], ta.w);
             st[i] = pending[i] ? ST_NOT_FOUND : ST_INVALID;
             lvl2[i] = false;
@@ -188,14 +196,17 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                     const bool live = r[i] >= 0;
                     if constexpr (LOOKUP) {
                         bool m, le;
-                        probe_chunk<W, FPW0>(v[i], e[i], m, le);
+                        int mpos = -1;
+                        if constexpr (SLOTS)
+                            probe_chunk_pos<W, FPW0>(v[i], e[i], m, le, mpos);
+                        else
+                            probe_chunk<W, FPW0>(v[i], e[i], m, le);
                         const uint32_t bm = __ballot_sync(0xffffffffu, live && m) & tmask;
                         const uint32_t be = __ballot_sync(0xffffffffu, live && le) & last_lane;
                         int y = 0;  // the matching slot's position in the bucket
                         if (want_slots) {
                             const int lm = bm ? __ffs(bm) - 1 - tbase : 0;
-                            y = lm * W * FPW0 +
-                                tile_shfl<T>(match_field<W, FPW0>(v[i], e[i]), lm);
+                            y = lm * W * FPW0 + tile_shfl<T>(mpos, lm);
                         }
                         if (tl == r[i]) {
                             n_probe++;
@@ -203,6 +214,8 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                                 st[i] = ST_FOUND;
                                 pending[i] = false;
                                 slot_of[i] = (uint64_t)a0[i] * B0 + (uint64_t)y;
+                                if (moves && slot_of[i] < ch.kv->nstore)
+                                    vpre[i] = kv_read(ch.kv->store, slot_of[i], ch.kv->vbytes);
                             } else if (be) {
                                 pending[i] = false;  // NOT_FOUND
                             } else {
@@ -211,8 +224,11 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                         }
                     } else {
                         bool m;
-                        int fe;
-                        scan_chunk<W, FPW0>(v[i], e[i], m, fe);
+                        int fe, mpos = -1;
+                        if constexpr (SLOTS)
+                            scan_chunk_pos<W, FPW0>(v[i], e[i], m, fe, mpos);
+                        else
+                            scan_chunk<W, FPW0>(v[i], e[i], m, fe);
                         const uint32_t bm = __ballot_sync(0xffffffffu, live && m) & tmask;
                         const uint32_t be = __ballot_sync(0xffffffffu, live && fe >= 0) & tmask;
                         cli[i] = be ? __ffs(be) - 1 - tbase : 0;
@@ -221,8 +237,7 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                         if (want_slots) {
                             // the slot that answers: the match, else the one claimed
                             const int src = bm ? __ffs(bm) - 1 - tbase : cli[i];
-                            const int val = bm ? match_field<W, FPW0>(v[i], e[i]) : fe;
-                            y1[i] = src * W * FPW0 + tile_shfl<T>(val, src);
+                            y1[i] = src * W * FPW0 + tile_shfl<T>(bm ? mpos : fe, src);
                         }
                         bmv |= (bm ? 1u : 0u) << i;
                         bev |= (be ? 1u : 0u) << i;
@@ -314,9 +329,14 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                         load_relaxed<W>(pb, vb);
                     }
                     bool ma, mb;
-                    int fa, fb;
-                    scan_chunk_rt<W>(va, ya, FPW1, ma, fa);
-                    scan_chunk_rt<W>(vb, yb, FPW1, mb, fb);
+                    int fa, fb, pa_pos = -1, pb_pos = -1;
+                    if constexpr (SLOTS) {
+                        scan_chunk_rt_pos<W>(va, ya, FPW1, ma, fa, pa_pos);
+                        scan_chunk_rt_pos<W>(vb, yb, FPW1, mb, fb, pb_pos);
+                    } else {
+                        scan_chunk_rt<W>(va, ya, FPW1, ma, fa);
+                        scan_chunk_rt<W>(vb, yb, FPW1, mb, fb);
+                    }
                     const uint32_t bfound = __ballot_sync(0xffffffffu, live && (ma || mb)) & tmask;
                     // slot outputs: where the match sits (bucket b?, lane, field)
                     int mval = 0;
@@ -324,7 +344,7 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                     if (want_slots) {
                         const uint32_t bma = __ballot_sync(0xffffffffu, live && ma) & tmask;
                         mb_side = !bma;
-                        mval = ma ? match_field_rt<W>(va, ya, FPW1) : match_field_rt<W>(vb, yb, FPW1);
+                        mval = ma ? pa_pos : pb_pos;
                     }
                     const uint64_t lvl2_base = L0.nb * B0;
                     if constexpr (LOOKUP) {
@@ -339,6 +359,8 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                                 st[i] = ST_FOUND;
                                 slot_of[i] = lvl2_base + (uint64_t)(mb_side ? ab[i] : aa[i]) * B1 +
                                         (uint64_t)y;
+                                if (moves && slot_of[i] < ch.kv->nstore)
+                                    vpre[i] = kv_read(ch.kv->store, slot_of[i], ch.kv->vbytes);
                             }
                             pending[i] = false;
                         }
@@ -414,7 +436,15 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
             const int pos = i * 32 + lane;
             if (pos < ch.count) {
                 ch.status[ch.base + pos] = st[i];
-                if (want_slots) ch.slots[ch.base + pos] = slot_of[i];
+                if constexpr (SLOTS) {
+                    if (ch.slots) ch.slots[ch.base + pos] = slot_of[i];
+                    if (moves) {
+                        if (LOOKUP)
+                            kv_write(ch.kv->vout, ch.base + pos, ch.kv->vbytes, vpre[i]);
+                        else if (slot_of[i] < ch.kv->nstore)
+                            kv_write(ch.kv->store, slot_of[i], ch.kv->vbytes, vpre[i]);
+                    }
+                }
             }
             n_ops += pos < ch.count ? 1 : 0;
         }
@@ -427,12 +457,22 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
     }
 }
 
-template <int T, int FPW0, int I, bool LOOKUP, bool SLOTS = false>
+template <int T, int FPW0, int I, bool LOOKUP>
 __global__ void __launch_bounds__(256)
     k_iceberg_warp(TableArgs ta, const void *__restrict__ keys, uint64_t n,
-                   uint8_t *__restrict__ status, uint64_t *__restrict__ slots) {
-    SingleSource src{&ta, keys, status, slots, n, (uint64_t)32 * I};
-    iceberg_warp<T, FPW0, I, LOOKUP, SingleSource, SLOTS>(src, ta.ctr);
+                   uint8_t *__restrict__ status) {
+    SingleSource src{&ta, keys, status, nullptr, nullptr, n, (uint64_t)32 * I};
+    iceberg_warp<T, FPW0, I, LOOKUP, SingleSource, false>(src, ta.ctr);
+}
+
+// with slot outputs and value moves (one key per lane); held to 64 registers
+// so that four blocks share an SM, as for the plain engine
+template <int T, int FPW0, bool LOOKUP>
+__global__ void __launch_bounds__(256, 4)
+    k_iceberg_warp_slots(TableArgs ta, const void *__restrict__ keys, uint64_t n,
+                         uint8_t *__restrict__ status, uint64_t *__restrict__ slots, KVArgs kv) {
+    SingleSource src{&ta, keys, status, slots, &kv, n, 32};
+    iceberg_warp<T, FPW0, 1, LOOKUP, SingleSource, true>(src, ta.ctr);
 }
 
 // one persistent launch over many tables; shared memory holds the prefix of

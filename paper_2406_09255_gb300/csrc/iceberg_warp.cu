@@ -13,7 +13,7 @@ static cudaError_t run_warp(const LaunchParams &lp, const TableArgs &ta, const v
                             uint64_t n, uint8_t *status, uint64_t *slots) {
     auto kern = k_iceberg_warp<T, FPW0, I, LOOKUP>;
     const int blocks = grid_blocks_warp((const void *)kern, lp, (n + I - 1) / I);
-    kern<<<blocks, lp.cta, 0, lp.stream>>>(ta, keys, n, status, slots);
+    kern<<<blocks, lp.cta, 0, lp.stream>>>(ta, keys, n, status);
     return cudaGetLastError();
 }
 
@@ -52,8 +52,10 @@ static cudaError_t by_tile(int T, int fpw0, const LaunchParams &lp, const TableA
 
 cudaError_t launch_iceberg_warp(int T, int fpw0, bool lookup, const LaunchParams &lp,
                                 const TableArgs &ta, const void *keys, uint64_t n,
-                                uint8_t *status, uint64_t *slots) {
-    if (slots) return launch_iceberg_warp_slots(T, fpw0, lookup, lp, ta, keys, n, status, slots);
+                                uint8_t *status, uint64_t *slots, const KVArgs *kv) {
+    if (slots || (kv && kv->store))
+        return launch_iceberg_warp_slots(T, fpw0, lookup, lp, ta, keys, n, status, slots,
+                                         kv ? *kv : KVArgs{});
     return lookup ? by_tile<true>(T, fpw0, lp, ta, keys, n, status, slots)
                   : by_tile<false>(T, fpw0, lp, ta, keys, n, status, slots);
 }

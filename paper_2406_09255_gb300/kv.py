@@ -1,8 +1,8 @@
 """Key-value map over an iceberg table: values live in a device array indexed
-by the stable slot of their key (iceberg entries never move once placed), so
-a put is a find-or-put that returns slots plus a scatter of the values, and a
-get is a lookup that returns slots plus a gather. Both moves are library
-kernels (cht_values_scatter / cht_values_gather)."""
+by the stable slot of their key (iceberg entries never move once placed). A
+put is a find-or-put whose answering lane also writes the value to the key's
+slot, and a get is a lookup whose answering lane reads it: one kernel each
+(cht_kv_put / cht_kv_get)."""
 from __future__ import annotations
 
 import torch
@@ -24,25 +24,28 @@ class KVMap:
         self.values = torch.zeros(table.slots, dtype=value_dtype, device=table.device)
         self._L = _lib.load()
 
-    def put(self, keys: torch.Tensor, values: torch.Tensor, stream=None):
-        """Insert or assign. Returns (status, slots). A key given twice in one
-        call keeps one of its values, which one is unspecified. FULL keys
-        store nothing."""
+    def put(self, keys: torch.Tensor, values: torch.Tensor, status=None, stream=None):
+        """Insert or assign, in one kernel (cht_kv_put). Returns the status
+        per key. A key given twice in one call keeps one of its values, which
+        one is unspecified. FULL keys store nothing."""
         if values.dtype != self.values.dtype or values.numel() != keys.numel():
             raise ValueError("one value of the map's dtype per key")
+        keys, status = self.table._prep(keys, status)
         values = values.contiguous()
-        status, slots = self.table.find_or_put(keys, stream=stream, slots=True)
-        _lib.check(self._L.cht_values_scatter(slots.data_ptr(), keys.numel(), values.data_ptr(),
-                                              self.value_bytes, self.values.data_ptr(),
-                                              self.values.numel(), _stream_handle(stream)))
-        return status, slots
+        _lib.check(self._L.cht_kv_put(self.table._h, keys.data_ptr(), keys.numel(),
+                                      values.data_ptr(), self.value_bytes, self.values.data_ptr(),
+                                      self.values.numel(), status.data_ptr(),
+                                      _stream_handle(stream)))
+        return status
 
-    def get(self, keys: torch.Tensor, stream=None):
-        """Returns (values, status): zero values for keys not found."""
-        status, slots = self.table.find(keys, stream=stream, slots=True)
-        out = torch.empty(keys.numel(), dtype=self.values.dtype, device=self.table.device)
-        _lib.check(self._L.cht_values_gather(slots.data_ptr(), keys.numel(),
-                                             self.values.data_ptr(), self.value_bytes,
-                                             self.values.numel(), out.data_ptr(),
-                                             _stream_handle(stream)))
+    def get(self, keys: torch.Tensor, status=None, out=None, stream=None):
+        """Values by key, in one kernel (cht_kv_get). Returns (values, status):
+        zero values for keys not found."""
+        keys, status = self.table._prep(keys, status)
+        if out is None:
+            out = torch.empty(keys.numel(), dtype=self.values.dtype, device=self.table.device)
+        _lib.check(self._L.cht_kv_get(self.table._h, keys.data_ptr(), keys.numel(),
+                                      self.values.data_ptr(), self.value_bytes,
+                                      self.values.numel(), out.data_ptr(), status.data_ptr(),
+                                      _stream_handle(stream)))
         return out, status

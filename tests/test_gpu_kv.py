@@ -135,12 +135,12 @@ def test_kv_map_put_get_assign():
     kv = Pm.KVMap(t, torch.int64)
     keys = W.unique_keys(0, 100_000, 40, 808).to(DEV)
     vals = torch.arange(100_000, dtype=torch.int64, device=DEV) * 3 + 1
-    st, _ = kv.put(keys, vals)
+    st = kv.put(keys, vals)
     assert bool((st == Pm.PUT).all())
     got, gst = kv.get(keys)
     assert bool((gst == Pm.FOUND).all()) and torch.equal(got, vals)
     half = keys[::2]
-    st2, _ = kv.put(half, -vals[::2])
+    st2 = kv.put(half, -vals[::2])
     assert bool((st2 == Pm.FOUND).all())
     got, _ = kv.get(keys)
     assert torch.equal(got[::2], -vals[::2]) and torch.equal(got[1::2], vals[1::2])
@@ -163,3 +163,37 @@ def test_slots_unsupported_on_cuckoo():
         t.find(k, slots=True)
     with pytest.raises(ValueError):
         Pm.KVMap(t)
+
+
+@pytest.mark.parametrize("T", [4, 8])
+def test_kv_sequential_values_at_oracle_slots(T):
+    """One tile, keys in input order (ordered engine): each value lands at
+    the oracle's slot for its key, a repeated key keeps the value of its last
+    occurrence, FULL keys store nothing, and get reads every stored value
+    back (zero for keys never stored)."""
+    Pm = P()
+    t = Pm.Table(Pm.ICEBERG, 32, 1 << 4, 1 << 2, key_bytes=4, fields_per_word=2,
+                 fields_per_word_backyard=2, seed=3, tile=T, max_tiles=1, cta_threads=64)
+    kv = Pm.KVMap(t, torch.int64)
+    o = mirror(t)
+    fresh = W.unique_keys(0, int(1.1 * t.slots), 32, 5)
+    rng = np.random.default_rng(2)
+    keys = torch.cat([fresh, fresh[torch.from_numpy(rng.integers(0, len(fresh), 300))]])
+    keys = keys[torch.from_numpy(rng.permutation(len(keys)))]
+    vals = torch.arange(len(keys), dtype=torch.int64) * 7 + 11
+    st = kv.put(dev_keys(keys, 4), vals.to(DEV)).cpu().numpy()
+    kn = keys.numpy().astype(np.uint64)
+    ost = o.insert(kn)
+    assert (st == ost).all() and (ost == oracle.FULL).sum() > 0
+    store = kv.values.cpu().numpy()
+    last = {}
+    for k, v, s_ in zip(kn.tolist(), vals.numpy().tolist(), ost.tolist()):
+        if s_ in (oracle.FOUND, oracle.PUT):
+            last[k] = v
+    loc = o.locate(np.array(list(last), dtype=np.uint64))
+    assert (store[loc.astype(np.int64)] == np.array(list(last.values()))).all()
+    got, gst = kv.get(dev_keys(keys, 4))
+    got, gst = got.cpu().numpy(), gst.cpu().numpy()
+    want = np.array([last.get(k, 0) for k in kn.tolist()])
+    assert (got == want).all()
+    assert ((gst == Pm.FOUND) == np.array([k in last for k in kn.tolist()])).all()

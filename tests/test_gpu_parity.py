@@ -429,3 +429,55 @@ def test_random_read_utility_reads_every_block_size():
                     tot += host[base + k]
                 want ^= np.bitwise_xor.reduce(tot)
         assert (int(sink.item()) & M) == int(want), bb
+
+
+def test_iceberg_2e22_full_size_stream():
+    """The find-or-put stream workload at full size (2^22 + 2^19 buckets,
+    150,994,944 slots, 48-bit keys; 80 % find-or-put / 20 % lookups, half
+    first-seen keys, half Zipf repeats), in the benchmark's 2^22-op batches
+    up to fill ~0.8: every find-or-put is PUT exactly once per distinct key
+    and FOUND otherwise, every lookup answers membership at that point of
+    the stream, the stored set is the set of keys put, Theorem 1's
+    invariants hold on the GPU's table, and a sample re-checked by the
+    oracle on that table agrees."""
+    P = cht()
+    t = P.Table(P.ICEBERG, 48, 1 << 22, 1 << 19, seed=3000)
+    assert t.slots == 150994944
+    max_distinct = int(0.8 * t.slots)
+    n_ops = int(max_distinct / 0.4)
+    keys, is_find, _ = W.fop_stream(n_ops, 48, W.SEED_BASE + 3, max_distinct=max_distinct,
+                                    rng_seed=3, device=DEV)
+    B = 1 << 22
+    st = torch.empty(B, dtype=torch.uint8, device=DEV)
+    seen = torch.empty(0, dtype=torch.int64, device=DEV)
+    puts = 0
+    for s0 in range(0, n_ops, B):
+        k, f = keys[s0:s0 + B], is_find[s0:s0 + B]
+        kf, kl = k[~f].contiguous(), k[f].contiguous()
+        sf = t.find_or_put(kf, status=st[: kf.numel()])
+        new = torch.unique(kf)
+        fresh = new[~torch.isin(new, seen)]
+        # exactly one PUT per key not seen before, FOUND for everything else
+        assert bool(((sf == P.PUT) | (sf == P.FOUND)).all())
+        put_keys = kf[sf == P.PUT]
+        assert put_keys.numel() == fresh.numel()
+        assert torch.equal(torch.sort(put_keys)[0], torch.sort(fresh)[0])
+        puts += fresh.numel()
+        seen = torch.sort(torch.cat([seen, fresh]))[0]
+        sl = t.find(kl, status=st[kf.numel(): kf.numel() + kl.numel()])
+        assert torch.equal(sl == P.FOUND, torch.isin(kl, seen))
+    assert puts == seen.numel() and puts > 0.7 * t.slots
+    stored, cnt = t.enumerate()
+    assert cnt == puts
+    assert torch.equal(torch.sort(stored)[0], seen)
+    del stored, keys, is_find
+    d = dump_into(mirror(t), t)
+    assert d.check_entries() == 0 and d.check_order_property() == 0 and d.check_prefix() == 0
+    g = torch.Generator(device=DEV)
+    g.manual_seed(1)
+    sample = torch.cat([seen[torch.randint(0, seen.numel(), (100000,), device=DEV, generator=g)],
+                        W.keys_at(torch.arange(100000, device=DEV) + (1 << 46), 48,
+                                  W.SEED_BASE + 3)])
+    got = t.find(sample).cpu().numpy()
+    assert (d.find(sample.cpu().numpy().view(np.uint64)) == got).all()
+    assert t.error_flags() == 0
