@@ -82,13 +82,19 @@ class Server:
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(2)]
         self.waves = 0
         self.launches = 0
+        self._budget = None  # (keys, time taken)
 
     # -- admission ------------------------------------------------------------
-    def _budget_keys(self) -> int:
-        free, total = torch.cuda.mem_get_info(self.dev)
-        usable = max(0, free - self.hbm_reserve * total)
-        # per admitted key: its status byte plus staging of fused launches
-        return int(min(self.max_wave_keys, usable // 16))
+    def _budget_keys(self, refresh_s: float = 0.01) -> int:
+        """Keys a wave may admit given free HBM (re-read at most every
+        refresh_s: the query is a driver call that costs the served loop)."""
+        now = time.perf_counter()
+        if self._budget is None or now - self._budget[1] > refresh_s:
+            free, total = torch.cuda.mem_get_info(self.dev)
+            usable = max(0, free - self.hbm_reserve * total)
+            # per admitted key: its status byte plus staging of fused launches
+            self._budget = (int(min(self.max_wave_keys, usable // 16)), now)
+        return self._budget[0]
 
     def plan(self, requests: list[Request], seed: int = 0) -> list[Request]:
         """Give every request its keys, in arrival order: fresh keys take the
@@ -165,9 +171,11 @@ class Server:
             inflight = still
             if not pending or len(inflight) >= 2:
                 if not pending and nxt < len(reqs) and not inflight and realtime:
-                    time.sleep(max(0.0, min(0.001, reqs[nxt].arrival - now)))
-                elif inflight:
-                    time.sleep(0)
+                    # idle: sleep towards the next arrival, but spin through
+                    # its last 200 us (sleeping is too coarse to admit on time)
+                    gap = reqs[nxt].arrival - now
+                    if gap > 2e-4:
+                        time.sleep(min(0.001, gap - 2e-4))
                 continue
             # form a wave: per table, a run of lookups or one write request
             budget = self._budget_keys()
