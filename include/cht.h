@@ -98,14 +98,17 @@ typedef struct cht_table cht_table; /* opaque host handle */
  * max_tiles             upper bound on tiles that take work (0 = no bound).
  *                       With max_tiles = 1 a single tile processes the keys
  *                       strictly in input order (a sequential run).
- * lookups_in_flight     bucket loads a tile keeps in flight in cht_find on
- *                       cuckoo tables: 1, 4 or 8 (0 = 4). With 1 each tile
- *                       walks its pending keys one load at a time; with 4 or
- *                       8 every lane holds a key, each round probes all of a
- *                       tile's keys with that many loads issued back to back,
- *                       and answered lanes take the next key (a stream of
- *                       fully packed rounds). Answers and probe counts are
- *                       the same for every value.
+ * lookups_in_flight     bucket loads a tile keeps in flight in cht_find and
+ *                       cht_insert on cuckoo tables: 1, 4 or 8 (0 = 4). With
+ *                       1 each tile walks its pending keys one load at a
+ *                       time (puts: chunks of items_per_thread keys per
+ *                       lane); with 4 or 8 every lane holds a key, each
+ *                       round takes one step of all of a tile's keys with
+ *                       that many loads issued back to back (puts also issue
+ *                       that many claims before reading any), and answered
+ *                       lanes take the next key (a stream of fully packed
+ *                       rounds). Lookup answers and probe counts are the
+ *                       same for every value. Iceberg operations ignore it.
  */
 typedef struct cht_config {
     int32_t kind;
