@@ -457,8 +457,10 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
     }
 }
 
+// five blocks per SM (48 registers): measured 5-8 % faster than four blocks
+// with fewer spills, and faster than six blocks with more
 template <int T, int FPW0, int I, bool LOOKUP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)
     k_iceberg_warp(TableArgs ta, const void *__restrict__ keys, uint64_t n,
                    uint8_t *__restrict__ status) {
     SingleSource src{&ta, keys, status, nullptr, nullptr, n, (uint64_t)32 * I};
