@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -77,7 +78,10 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples go to CHT_CLOCKS_DIR (default: the system temp dir); the
+        # JSON line carries their summary
+        self.path = os.path.join(os.environ.get("CHT_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"cht_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
