@@ -24,27 +24,6 @@
 
 namespace cht {
 
-// field_op_issue / claim_finish with the packing known only at run time
-__device__ __forceinline__ uint64_t claim_issue_rt(int fpw, uint64_t *wp, int f, uint64_t snap,
-                                                   uint64_t entry, uint64_t &expected) {
-    switch (fpw) {
-        case 1: return field_op_issue<1>(false, wp, f, snap, entry, expected);
-        case 2: return field_op_issue<2>(false, wp, f, snap, entry, expected);
-        case 3: return field_op_issue<3>(false, wp, f, snap, entry, expected);
-        default: return field_op_issue<4>(false, wp, f, snap, entry, expected);
-    }
-}
-__device__ __forceinline__ bool claim_finish_rt(int fpw, uint64_t *wp, int f, uint64_t old,
-                                                uint64_t expected, uint64_t entry, uint64_t &seen,
-                                                int &fails) {
-    switch (fpw) {
-        case 1: return claim_finish<1>(wp, f, old, expected, entry, seen, fails);
-        case 2: return claim_finish<2>(wp, f, old, expected, entry, seen, fails);
-        case 3: return claim_finish<3>(wp, f, old, expected, entry, seen, fails);
-        default: return claim_finish<4>(wp, f, old, expected, entry, seen, fails);
-    }
-}
-
 // a warp's share of the keys: up to 32 * I keys of one table
 struct WarpChunk {
     const TableArgs *ta;
