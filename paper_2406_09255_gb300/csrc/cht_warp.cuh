@@ -459,8 +459,8 @@ __global__ void __launch_bounds__(256, 4)
 // one persistent launch over many tables; shared memory holds the prefix of
 // the tables' chunk counts (chunks of 32 * I keys), scanned by the first warp
 template <int T, int FPW0, int I, bool LOOKUP>
-__global__ void __launch_bounds__(256)
-    k_iceberg_batch(const BatchDesc *__restrict__ bd, int count, unsigned long long *ctr) {
+__device__ __forceinline__ void iceberg_batch_body(const BatchDesc *__restrict__ bd, int count,
+                                                   unsigned long long *ctr) {
     extern __shared__ uint64_t smem[];
     uint64_t *prefix = smem;  // count + 1 entries
     const uint64_t per = (uint64_t)32 * I;
@@ -483,6 +483,19 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     BatchSource src{bd, prefix, count, per};
     iceberg_warp<T, FPW0, I, LOOKUP>(src, ctr);
+}
+
+template <int T, int FPW0, int I, bool LOOKUP>
+__global__ void __launch_bounds__(256)
+    k_iceberg_batch(const BatchDesc *__restrict__ bd, int count, unsigned long long *ctr) {
+    iceberg_batch_body<T, FPW0, I, LOOKUP>(bd, count, ctr);
+}
+
+// one key per lane: five blocks per SM, as for the single-table engine
+template <int T, int FPW0, bool LOOKUP>
+__global__ void __launch_bounds__(256, 5)
+    k_iceberg_batch1(const BatchDesc *__restrict__ bd, int count, unsigned long long *ctr) {
+    iceberg_batch_body<T, FPW0, 1, LOOKUP>(bd, count, ctr);
 }
 
 }  // namespace cht

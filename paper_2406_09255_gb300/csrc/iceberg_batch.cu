@@ -13,7 +13,11 @@ static size_t batch_smem(int count) { return (size_t)((count + 2) & ~1) * 8; }
 template <int T, int FPW0, int I, bool LOOKUP>
 static cudaError_t run_batch(const LaunchParams &lp, const BatchDesc *bd, int count,
                              uint64_t total_chunks, unsigned long long *ctr) {
-    auto kern = k_iceberg_batch<T, FPW0, I, LOOKUP>;
+    void (*kern)(const BatchDesc *, int, unsigned long long *);
+    if constexpr (I == 1)
+        kern = k_iceberg_batch1<T, FPW0, LOOKUP>;
+    else
+        kern = k_iceberg_batch<T, FPW0, I, LOOKUP>;
     const size_t smem = batch_smem(count);
     const uint64_t warps_per_block = lp.cta / 32;
     uint64_t need = (total_chunks + warps_per_block - 1) / warps_per_block;
