@@ -19,9 +19,12 @@
  * 64-bit slots and is the paper's non-compact baseline (Section 5.1).
  *
  * Conventions for every call below:
- *  - Pointers named d_* are DEVICE pointers on the current CUDA device. The
- *    caller owns all memory: the table storage, key arrays and outputs. The
- *    library allocates no device memory.
+ *  - Pointers named d_* are addresses the current CUDA device can access:
+ *    device memory, or page-locked host memory, which the kernels then read
+ *    and write directly over the CPU-GPU link (for key, status, slot and
+ *    value arrays; table storage must be device memory). The caller owns all
+ *    memory: the table storage, key arrays and outputs. The library
+ *    allocates no device memory.
  *  - stream is a cudaStream_t passed as an opaque pointer (NULL = the legacy
  *    default stream). Calls only enqueue work and return; results are valid
  *    once the stream has been synchronised.

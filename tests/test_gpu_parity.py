@@ -481,3 +481,33 @@ def test_iceberg_2e22_full_size_stream():
     got = t.find(sample).cpu().numpy()
     assert (d.find(sample.cpu().numpy().view(np.uint64)) == got).all()
     assert t.error_flags() == 0
+
+
+def test_host_resident_keys_and_statuses():
+    """Key and status arrays in page-locked host memory: the kernels read the
+    keys and write the statuses over the CPU-GPU link, with the same results
+    as device-resident arrays (cuckoo put and lookup, iceberg find-or-put)."""
+    from paper_2406_09255_gb300 import _lib
+    L = _lib.load()
+    P = cht()
+    s = torch.cuda.current_stream().cuda_stream
+    t = P.Table(P.CUCKOO, 40, 1 << 12, seed=77)
+    n = int(0.8 * t.slots)
+    keys = W.unique_keys(0, n, 40, 31)
+    hk = keys.pin_memory()
+    hs = torch.zeros(n, dtype=torch.uint8).pin_memory()
+    _lib.check(L.cht_insert(t._h, hk.data_ptr(), n, hs.data_ptr(), None, s))
+    torch.cuda.synchronize()
+    assert bool((hs == P.PUT).all())
+    q, present = W.find_queries(n, 50000, 0.5, 40, 31, n)
+    hq, hqs = q.pin_memory(), torch.zeros(q.numel(), dtype=torch.uint8).pin_memory()
+    _lib.check(L.cht_find(t._h, hq.data_ptr(), q.numel(), hqs.data_ptr(), s))
+    torch.cuda.synchronize()
+    assert torch.equal(hqs, t.find(q.to(DEV)).cpu())
+    assert torch.equal(hqs == P.FOUND, present)
+    ti = P.Table(P.ICEBERG, 40, 1 << 10, 1 << 7, seed=78)
+    k2 = torch.cat([keys[:20000], keys[:5000]])
+    hk2, hs2 = k2.pin_memory(), torch.zeros(k2.numel(), dtype=torch.uint8).pin_memory()
+    _lib.check(L.cht_find_or_put(ti._h, hk2.data_ptr(), k2.numel(), hs2.data_ptr(), s))
+    torch.cuda.synchronize()
+    assert int((hs2 == P.PUT).sum()) == 20000 and bool((hs2[20000:] == P.FOUND).all())
