@@ -510,4 +510,6 @@ def test_host_resident_keys_and_statuses():
     hk2, hs2 = k2.pin_memory(), torch.zeros(k2.numel(), dtype=torch.uint8).pin_memory()
     _lib.check(L.cht_find_or_put(ti._h, hk2.data_ptr(), k2.numel(), hs2.data_ptr(), s))
     torch.cuda.synchronize()
-    assert int((hs2 == P.PUT).sum()) == 20000 and bool((hs2[20000:] == P.FOUND).all())
+    # one PUT per distinct key (which occurrence puts is up to the schedule)
+    assert int((hs2 == P.PUT).sum()) == 20000
+    assert bool(((hs2 == P.PUT) | (hs2 == P.FOUND)).all())
