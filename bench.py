@@ -306,7 +306,7 @@ def run_random_read(args, dev):
     print(json.dumps(out))
 
 
-def run_e2e(wl, steps, warmup):
+def run_e2e(wl, steps, warmup, direct=False):
     """The same step through the host-buffer API: each step copies its keys and
     queries from pinned host memory and reads every status and the enumerated
     keys back."""
@@ -325,7 +325,25 @@ def run_e2e(wl, steps, warmup):
     h_st_find = [[torch.empty(wl.nq, dtype=torch.uint8, pin_memory=True) for _ in row]
                  for row in wl.queries]
     h_enum = torch.empty(wl.slots, dtype=torch.int64, pin_memory=True)
-    pipe = HostPipeline(wl.t, chunk_keys=1 << 24, depth=3)
+    pipe = HostPipeline(wl.t, chunk_keys=1 << 24, depth=3) if not direct else None
+    s_direct = torch.cuda.Stream(device=wl.dev) if direct else None
+    cnt_dev = torch.zeros(1, dtype=torch.int64, device=wl.dev)
+
+    def step_direct():
+        # the kernels read keys from and write statuses / enumerated keys to
+        # the pinned host buffers directly over the CPU-GPU link
+        t = wl.t
+        t.clear(stream=s_direct)
+        prev = 0
+        for fi, n in enumerate(wl.n_f):
+            t.insert(h_keys[prev:n], status=h_st_ins[prev:n], stream=s_direct)
+            prev = n
+            for hi in range(len(wl.spec["hits"])):
+                t.find(h_q[fi][hi], status=h_st_find[fi][hi], stream=s_direct)
+        with torch.cuda.stream(s_direct):
+            _, cnt = t.enumerate(cap=wl.slots, out=h_enum, count=cnt_dev, stream=s_direct)
+        s_direct.synchronize()
+        return cnt
 
     def step():
         # every operation is queued on the pipeline's streams without waiting;
@@ -345,24 +363,34 @@ def run_e2e(wl, steps, warmup):
         pipe.sync()
         return cnt
 
+    run = step_direct if direct else step
     for _ in range(warmup):
-        step()
+        run()
     torch.cuda.synchronize()
-    pipe.h2d_bytes = pipe.d2h_bytes = pipe.launches = 0
+    if pipe is not None:
+        pipe.h2d_bytes = pipe.d2h_bytes = pipe.launches = 0
     enum_bytes = 0
     t0 = time.perf_counter()
     for _ in range(steps):
-        enum_bytes += 8 * step() + 8
+        enum_bytes += 8 * run() + 8
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    if direct:
+        h2d = 8 * (wl.n_max + wl.nq * len(wl.n_f) * len(wl.spec["hits"]))
+        d2h = wl.n_max + wl.nq * len(wl.n_f) * len(wl.spec["hits"])
+        api = ("cht_insert/cht_find/cht_enumerate on pinned host buffers: the kernels read "
+               "keys and write statuses and enumerated keys over the CPU-GPU link")
+    else:
+        h2d, d2h = pipe.h2d_bytes // steps, pipe.d2h_bytes // steps
+        api = ("HostPipeline over cht_insert/cht_find with pinned host buffers, 2^24-key "
+               "chunks, 3 staging buffers, separate H2D / compute / D2H streams")
     return {
         "value": wl.ops_per_step * steps / dt / 1e6,
         "unit": "Mops/s",
-        "h2d_bytes_per_step": pipe.h2d_bytes // steps,
-        "d2h_bytes_per_step": (pipe.d2h_bytes + enum_bytes) // steps,
+        "h2d_bytes_per_step": h2d,
+        "d2h_bytes_per_step": d2h + enum_bytes // steps,
         "ms_per_step": dt / steps * 1e3,
-        "api": "HostPipeline over cht_insert/cht_find with pinned host buffers, 2^24-key "
-               "chunks, 3 staging buffers, separate H2D / compute / D2H streams",
+        "api": api,
     }
 
 

@@ -117,13 +117,28 @@ class Table:
 
     # -- operations -----------------------------------------------------------
     def _prep(self, keys: torch.Tensor, out):
-        if keys.device != self.device:
-            raise ValueError(f"keys must be on {self.device} (got {keys.device})")
+        """Keys on the table's device, or in page-locked host memory: the
+        kernels then read them (and write the statuses, which must be
+        page-locked host memory too) directly over the CPU-GPU link. As with
+        device outputs, host outputs are valid once the stream has been
+        synchronised."""
+        host = keys.device.type == "cpu"
+        if host and not keys.is_pinned():
+            raise ValueError("host keys must be in page-locked memory (pin_memory())")
+        if not host and keys.device != self.device:
+            raise ValueError(f"keys must be on {self.device} or pinned host memory "
+                             f"(got {keys.device})")
         if keys.dtype != self.key_dtype:
             raise ValueError(f"keys must be {self.key_dtype} for {self.cfg.key_bytes}-byte keys")
-        keys = keys.contiguous()
+        if not keys.is_contiguous():
+            if host:
+                raise ValueError("pinned host keys must be contiguous")
+            keys = keys.contiguous()
         if out is None:
-            out = torch.empty(keys.numel(), dtype=torch.uint8, device=self.device)
+            out = (torch.empty(keys.numel(), dtype=torch.uint8, pin_memory=True) if host
+                   else torch.empty(keys.numel(), dtype=torch.uint8, device=self.device))
+        elif host != (out.device.type == "cpu") or (host and not out.is_pinned()):
+            raise ValueError("statuses must live where the keys live (device or pinned host)")
         return keys, out
 
     def insert(self, keys: torch.Tensor, status=None, dropped=None, stream=None):

@@ -513,3 +513,30 @@ def test_host_resident_keys_and_statuses():
     # one PUT per distinct key (which occurrence puts is up to the schedule)
     assert int((hs2 == P.PUT).sum()) == 20000
     assert bool(((hs2 == P.PUT) | (hs2 == P.FOUND)).all())
+
+
+def test_table_methods_accept_pinned_host_tensors():
+    """Table.insert / find / find_or_put / enumerate with page-locked host
+    tensors give the same answers as with device tensors; unpinned host
+    tensors are refused."""
+    P = cht()
+    t = P.Table(P.CUCKOO, 40, 1 << 10, seed=5)
+    keys = W.unique_keys(0, 30000, 40, 77)
+    # host results are valid once the stream has been synchronised
+    st = t.insert(keys.pin_memory())
+    torch.cuda.synchronize()
+    assert st.device.type == "cpu" and st.is_pinned() and bool((st == P.PUT).all())
+    q, present = W.find_queries(30000, 20000, 0.5, 40, 77, 30000)
+    fq = t.find(q.pin_memory())
+    torch.cuda.synchronize()
+    assert torch.equal(fq == P.FOUND, present)
+    out = torch.empty(t.slots, dtype=torch.int64).pin_memory()
+    stored, cnt = t.enumerate(out=out)
+    assert cnt == 30000 and torch.equal(torch.sort(stored)[0], torch.sort(keys)[0])
+    with pytest.raises(ValueError):
+        t.find(q)  # pageable host memory
+    ti = P.Table(P.ICEBERG, 40, 1 << 9, 1 << 6, seed=6)
+    k2 = torch.cat([keys[:5000], keys[:1000]]).pin_memory()
+    s2 = ti.find_or_put(k2)
+    torch.cuda.synchronize()
+    assert int((s2 == P.PUT).sum()) == 5000 and bool(((s2 == P.PUT) | (s2 == P.FOUND)).all())
