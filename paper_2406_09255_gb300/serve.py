@@ -56,6 +56,30 @@ class Request:
     status: torch.Tensor | None = None
 
 
+def form_wave(pending: list, budget: int) -> tuple[list, list]:
+    """Split the pending requests (in admission order) into the next wave and
+    the rest. Per table the wave takes a run of consecutive lookups or one
+    write request, and no request is taken past an earlier one of its table
+    that stays behind, so every table sees its requests in admission order.
+    The wave holds at most budget keys, but always at least one request.
+    Linear in the number of pending requests."""
+    wave, rest, used, taken = [], [], 0, {}
+    blocked = set()  # tables with an earlier request left for a later wave
+    for r in pending:
+        kind = "r" if r.op == FIND else "w"
+        cur = taken.get(r.table)
+        fits = used + r.n <= budget or not wave
+        ok = fits and (cur is None or (cur == "r" and kind == "r"))
+        if ok and r.table not in blocked:
+            wave.append(r)
+            used += r.n
+            taken[r.table] = kind
+        else:
+            rest.append(r)
+            blocked.add(r.table)
+    return wave, rest
+
+
 @dataclasses.dataclass
 class TableState:
     table: Table
@@ -177,23 +201,7 @@ class Server:
                     if gap > 2e-4:
                         time.sleep(min(0.001, gap - 2e-4))
                 continue
-            # form a wave: per table, a run of lookups or one write request
-            budget = self._budget_keys()
-            wave, used, taken, rest = [], 0, {}, []
-            blocked = set()  # tables with an earlier request left for a later wave
-            for r in pending:
-                kind = "r" if r.op == FIND else "w"
-                cur = taken.get(r.table)
-                fits = used + r.n <= budget or not wave
-                ok = fits and (cur is None or (cur == "r" and kind == "r"))
-                if ok and r.table not in blocked:
-                    wave.append(r)
-                    used += r.n
-                    taken[r.table] = kind
-                else:
-                    rest.append(r)
-                    blocked.add(r.table)
-            pending = rest
+            wave, pending = form_wave(pending, self._budget_keys())
             tnow = time.perf_counter() - t0
             for r in wave:
                 r.admitted = tnow
