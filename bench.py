@@ -15,6 +15,13 @@ are 128 * P + 8 + 1 (P = bucket probes the lookup makes, counted by the
 kernel's counters in an untimed pass over the same tables; one 128-byte line
 per probe, the 8-byte key, the 1-byte status); achieved = those bytes over
 the summed CUDA-event durations of the lookup launches in the timed region.
+Because probes are reads at data-dependent addresses, the line also reports
+the probe rate against the measured random-read rate of 128-byte lines
+(cht_random_read, after the timed region).
+
+Other workloads (--workload): the iceberg find-or-put stream, 256 fused
+tables, the served request loop, the key-value extension, iceberg slot
+widths, whole-key cuckoo tables and the random-read rate by block size.
 
 `--impl reference` times the sequential CPU oracle instead, on bounded
 samples of the same workload (the oracle of this repository stands in for
