@@ -1,5 +1,6 @@
-// cht_cuckoo_warp.cuh - warp-batched compact cuckoo put (Algorithm 4) for
-// unordered runs.
+// cht_cuckoo_warp.cuh - compact cuckoo put (Algorithm 4) for unordered
+// runs: the warp-batched chunk form described here, and the stream form
+// (k_cuckoo_insert_stream, the default) described at its definition below.
 //
 // A warp takes chunks of 32 * I keys; every lane holds I keys "in hand", each
 // with its hash index j and step count c. In each pass, tiles of T lanes
