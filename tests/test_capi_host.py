@@ -133,3 +133,33 @@ def test_value_moves_reject_bad_arguments_without_a_launch(lib):
     assert L.cht_values_gather(ctypes.c_void_p((1 << 20) + 4), 10, fake, 8, 100, fake,
                                None) == lib.CHT_ERR_INVALID
     assert L.cht_values_scatter(fake, 0, fake, 8, fake, 100, None) == lib.CHT_OK  # empty: nothing to do
+
+
+def test_null_handles_rejected_on_the_host(lib):
+    """Every call taking a table or batch handle refuses NULL with
+    CHT_ERR_INVALID before touching the GPU; destroy accepts NULL."""
+    L = lib.load()
+    z = ctypes.c_void_p(0)
+    p = ctypes.c_void_p(1 << 20)  # never dereferenced: the handle check comes first
+    INV = lib.CHT_ERR_INVALID
+    calls = [
+        lambda: L.cht_clear(z, None),
+        lambda: L.cht_insert(z, p, 1, p, None, None),
+        lambda: L.cht_find(z, p, 1, p, None),
+        lambda: L.cht_find_or_put(z, p, 1, p, None),
+        lambda: L.cht_find_or_put_slots(z, p, 1, p, p, None),
+        lambda: L.cht_find_slots(z, p, 1, p, p, None),
+        lambda: L.cht_kv_put(z, p, 1, p, 8, p, 10, p, None),
+        lambda: L.cht_kv_get(z, p, 1, p, 8, 10, p, p, None),
+        lambda: L.cht_enumerate(z, p, 1, p, None),
+        lambda: L.cht_set_counters(z, None),
+        lambda: L.cht_batch_launch(z, None),
+        lambda: L.cht_batch_replay(z, None),
+        lambda: L.cht_batch_clear(z, None),
+        lambda: L.cht_batch_capture(z, None),
+    ]
+    for c in calls:
+        assert c() == INV
+        assert L.cht_last_error().decode()
+    assert L.cht_destroy(z) == lib.CHT_OK
+    assert L.cht_batch_destroy(z) == lib.CHT_OK
