@@ -163,3 +163,31 @@ def test_null_handles_rejected_on_the_host(lib):
         assert L.cht_last_error().decode()
     assert L.cht_destroy(z) == lib.CHT_OK
     assert L.cht_batch_destroy(z) == lib.CHT_OK
+
+
+def test_batch_scratch_and_create_validation_on_the_host(lib):
+    """cht_batch_scratch_bytes gives one fixed-size descriptor per table for
+    1..16384 tables (a multiple of 16 bytes, so descriptors stay aligned) and
+    0 outside; cht_batch_create checks its count, op, scratch alignment and
+    size before it looks at any table."""
+    L = lib.load()
+    d = L.cht_batch_scratch_bytes(1)
+    assert d > 0 and d % 16 == 0
+    assert L.cht_batch_scratch_bytes(256) == 256 * d
+    assert L.cht_batch_scratch_bytes(0) == 0 and L.cht_batch_scratch_bytes(16385) == 0
+    p = ctypes.c_void_p(1 << 20)  # never dereferenced: every call fails validation
+    arr = (ctypes.c_void_p * 1)(p)
+    ns = (ctypes.c_size_t * 1)(10)
+    out = ctypes.c_void_p(0)
+    INV = lib.CHT_ERR_INVALID
+
+    def create(count=1, op=0, scratch=p, nbytes=d):
+        return L.cht_batch_create(arr, arr, ns, arr, count, op, scratch, nbytes, None,
+                                  ctypes.byref(out))
+
+    assert create(count=0) == INV and "count" in L.cht_last_error().decode()
+    assert create(count=16385) == INV
+    assert create(op=7) == INV and "op" in L.cht_last_error().decode()
+    assert create(scratch=ctypes.c_void_p((1 << 20) + 8)) == INV
+    assert create(nbytes=d - 1) == lib.CHT_ERR_CAPACITY
+    assert out.value is None
