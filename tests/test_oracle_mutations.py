@@ -34,6 +34,12 @@ MUTATIONS = [
      "return (body << 2) | (uint64_t)(j + 1);", "return (body << 2) | (uint64_t)j;"),
     ("primary occupancy bit dropped",
      "return (body << 1) | 1ULL;", "return body << 1;"),
+    ("enumeration decodes secondary entries with the other hash",
+     "return c->compact ? orc_key_from(c, 1, x - 1, a, e >> 2) : e >> 2;",
+     "return c->compact ? orc_key_from(c, 1, 2 - x, a, e >> 2) : e >> 2;"),
+    ("enumeration decodes primary entries without the flag shift",
+     "return c->compact ? orc_key_from(c, 0, 0, a, e >> 1) : e >> 1;",
+     "return c->compact ? orc_key_from(c, 0, 0, a, e >> 2) : e >> 1;"),
 ]
 
 
