@@ -112,13 +112,33 @@ def tune_batch(batch, reps: int = 3, use_cache: bool = True, tiles=TILES, items=
     return dict(out, cached=False)
 
 
+def table_candidates(kind: int, op: str, current_in_flight: int, tiles=TILES, items=ITEMS,
+                     in_flight=None) -> list[tuple[int, int, int]]:
+    """(tile, items_per_thread, lookups_in_flight) shapes tune_table tries:
+    on cuckoo tables the chunk forms (one load in flight, every items value)
+    and the stream forms (4 or 8 loads in flight, items unused); iceberg
+    operations keep the table's in-flight setting, which they ignore."""
+    if in_flight is None:
+        in_flight = (1, 4, 8) if (kind == 0 and op != "find_or_put") else (current_in_flight,)
+    cands = []
+    for P in in_flight:
+        # items_per_thread matters to the chunk forms: cuckoo with one load in
+        # flight, and every iceberg operation
+        sweep_items = P == 1 or kind == 1
+        for T in tiles:
+            for I in (items if sweep_items else (1,)):
+                cands.append((T, I, P))
+    return cands
+
+
 def tune_table(table, op: str, keys: torch.Tensor, reps: int = 3, use_cache: bool = True,
                tiles=TILES, items=ITEMS, in_flight=None) -> dict:
     """Pick the launch shape for one operation on one table ("find", "insert"
-    or "find_or_put"); applies and returns it. Candidates are (tile,
-    items_per_thread) pairs with the table's lookups_in_flight and, on cuckoo
-    tables, also each tile with 4 or 8 loads in flight (the stream kernels,
-    which take no items_per_thread)."""
+    or "find_or_put"); applies and returns it. The candidates are those of
+    table_candidates: every (tile, items_per_thread) pair for iceberg
+    operations and for cuckoo's one-load form, plus each tile with 4 or 8
+    loads in flight on cuckoo tables (the stream kernels, which take no
+    items_per_thread)."""
     key = shape_key(op, [table])
     if use_cache:
         hit = _load_cache().get(key)
@@ -127,14 +147,8 @@ def tune_table(table, op: str, keys: torch.Tensor, reps: int = 3, use_cache: boo
                              lookups_in_flight=hit.get("in_flight",
                                                        table.cfg.lookups_in_flight))
             return dict(hit, cached=True)
-    if in_flight is None:
-        in_flight = (1, 4, 8) if (table.cfg.kind == 0 and op != "find_or_put") else (
-            table.cfg.lookups_in_flight,)
-    cands = []
-    for P in in_flight:
-        for T in tiles:
-            for I in (items if P == 1 else (1,)):
-                cands.append((T, I, P))
+    cands = table_candidates(table.cfg.kind, op, table.cfg.lookups_in_flight, tiles, items,
+                             in_flight)
     snap = table.storage.clone()
     status = torch.empty(keys.numel(), dtype=torch.uint8, device=keys.device)
     fn = getattr(table, op)
