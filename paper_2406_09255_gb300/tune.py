@@ -117,7 +117,8 @@ def table_candidates(kind: int, op: str, current_in_flight: int, tiles=TILES, it
     """(tile, items_per_thread, lookups_in_flight) shapes tune_table tries:
     on cuckoo tables the chunk forms (one load in flight, every items value)
     and the stream forms (4 or 8 loads in flight, items unused); iceberg
-    operations keep the table's in-flight setting, which they ignore."""
+    operations keep the table's in-flight setting, which they ignore, and
+    try every items value."""
     if in_flight is None:
         in_flight = (1, 4, 8) if (kind == 0 and op != "find_or_put") else (current_in_flight,)
     cands = []
