@@ -17,6 +17,15 @@ Parity status per function (see the tests that pin each one):
   cuckoo_insert / cuckoo_find: pinned by set semantics on brute-force tiny
       tables, the H=1 closed form (a plain bucketed table), and the exhaustive
       lookup.
+  check_prefix / check_entries / check_order_property / check_cuckoo_chain /
+      check_duplicates: pinned by hand-built tables that break one invariant
+      a known number of times (exact counts) and by a plain restatement of
+      Definition 1 on perturbed tables.
+  insert_concurrent (host-threaded model of the packed-word claim): pinned by
+      equality with the sequential operations on one thread and by Theorem 1
+      and key conservation under real races on many threads.
+  A mutation check plants plausible mistakes in all of the above; each is
+  caught by these pins.
 """
 from __future__ import annotations
 
@@ -44,8 +53,8 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_SO) >= os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
         return _SO
     tmp = _SO + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall",
-                           "-o", tmp, src])
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-Wall",
+                           "-pthread", "-o", tmp, src])
     os.replace(tmp, _SO)
     return _SO
 
@@ -100,6 +109,12 @@ def lib():
                 "orc_check_entries": (u64, [_cfgp, _u64p, _u64p]),
                 "orc_check_order_property": (u64, [_cfgp, _u64p, _u64p]),
                 "orc_check_cuckoo_chain": (u64, [_cfgp, _u64p]),
+                "orc_check_duplicates": (u64, [_cfgp, _u64p, _u64p]),
+                "orc_set_slot": (None, [_cfgp, i, _u64p, u64, i, u64]),
+                "orc_entry_of": (u64, [_cfgp, i, u64]),
+                "orc_bucket_of": (u64, [_cfgp, i, u64]),
+                "orc_concurrent_insert": (i, [_cfgp, _u64p, _u64p, _u64p, _sz, _u8p, _u64p, i,
+                                              _u64p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -196,6 +211,20 @@ class Table:
         t = self.t0 if level == 0 else self.t1
         return int(lib().orc_get_slot(self._cp, level, _p64(t), bucket, y))
 
+    def set_slot(self, level: int, bucket: int, y: int, value: int) -> None:
+        """Overwrite one slot (tests plant invariant violations with it)."""
+        t = self.t0 if level == 0 else self.t1
+        lib().orc_set_slot(self._cp, level, _p64(t), bucket, y, value)
+
+    def entry_of(self, x: int, k: int) -> int:
+        """Encoded entry of key k under choice x (cuckoo: hash index j;
+        iceberg: 0 primary, 1 / 2 the secondary choices)."""
+        return int(lib().orc_entry_of(self._cp, x, k))
+
+    def bucket_of(self, x: int, k: int) -> int:
+        """Bucket of key k under choice x (same x as entry_of)."""
+        return int(lib().orc_bucket_of(self._cp, x, k))
+
     # -- operations --------------------------------------------------------
     def insert(self, keys):
         """Cuckoo: Algorithm 4 per key. Iceberg: find-or-put. Returns
@@ -217,6 +246,23 @@ class Table:
     def find_or_put(self, keys):
         assert self.cfg.kind == ICEBERG
         return self.insert(keys)
+
+    def insert_concurrent(self, keys, threads: int):
+        """The host-threaded model: the kind's write operation (iceberg
+        find-or-put, cuckoo put) on `threads` threads at once, with
+        field-level compare-and-swap claims on packed words. Returns (status,
+        dropped, threads that ran concurrently, lost compare-and-swaps);
+        status 5 marks a key whose bounded retry gave up."""
+        k = _keys(keys)
+        st = np.zeros(len(k), dtype=np.uint8)
+        dr = np.zeros(len(k), dtype=np.uint64)
+        fails = ctypes.c_uint64(0)
+        ran = lib().orc_concurrent_insert(self._cp, _p64(self.t0), _p64(self.t1), _p64(k),
+                                          len(k), _p8(st), _p64(dr), threads,
+                                          ctypes.byref(fails))
+        if ran < 0:
+            raise ValueError("oracle: bad arguments to the threaded model")
+        return st, dr, int(ran), int(fails.value)
 
     def find(self, keys):
         k = _keys(keys)
@@ -273,6 +319,13 @@ class Table:
     def check_cuckoo_chain(self) -> int:
         assert self.cfg.kind == CUCKOO
         return int(lib().orc_check_cuckoo_chain(self._cp, _p64(self.t0)))
+
+    def check_duplicates(self) -> int:
+        return int(lib().orc_check_duplicates(self._cp, _p64(self.t0), _p64(self.t1)))
+
+    def check_prefix_level(self, level: int) -> int:
+        t = self.t0 if level == 0 else self.t1
+        return int(lib().orc_check_prefix(self._cp, level, _p64(t)))
 
     def load_words(self, t0: np.ndarray, t1: np.ndarray | None = None):
         """Replace the table contents with a dump (e.g. of a device table)."""

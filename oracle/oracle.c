@@ -217,8 +217,8 @@ uint64_t orc_get_slot(const orc_cfg *c, int level, const uint64_t *table,
     return (word >> ((y % fpw) * s)) & orc_low_mask(s);
 }
 
-static void orc_set_slot(const orc_cfg *c, int level, uint64_t *table,
-                         uint64_t bucket, int y, uint64_t v)
+void orc_set_slot(const orc_cfg *c, int level, uint64_t *table,
+                  uint64_t bucket, int y, uint64_t v)
 {
     int fpw = c->fpw[level];
     int s = 64 / fpw;
@@ -262,6 +262,19 @@ static const uint64_t *orc_level_table(int x, const uint64_t *t0,
                                        const uint64_t *t1)
 {
     return x == 0 ? t0 : t1;
+}
+
+/* the entry key k has under choice x and the bucket it goes to: for cuckoo x
+ * is the hash index j (level 0); for iceberg x = 0 is the primary bucket and
+ * x = 1, 2 the secondary ones */
+uint64_t orc_entry_of(const orc_cfg *c, int x, uint64_t k)
+{
+    return c->kind == 0 ? orc_cuckoo_entry(c, x, k) : orc_iceberg_entry(c, x, k);
+}
+
+uint64_t orc_bucket_of(const orc_cfg *c, int x, uint64_t k)
+{
+    return c->kind == 0 ? orc_address(c, 0, x, k) : orc_iceberg_bucket(c, x, k);
 }
 
 static int orc_bucket_contains(const orc_cfg *c, int level,
@@ -714,4 +727,302 @@ uint64_t orc_check_cuckoo_chain(const orc_cfg *c, const uint64_t *table)
                 }
         }
     return bad;
+}
+
+static int orc_cmp_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* no key is stored twice (Appendix A, the no-duplicates lemma; for cuckoo the
+ * set semantics of Section 3): the number of stored entries minus the number
+ * of distinct keys they decode to */
+uint64_t orc_check_duplicates(const orc_cfg *c, const uint64_t *t0,
+                              const uint64_t *t1)
+{
+    uint64_t n = orc_enumerate(c, t0, t1, NULL, 0);
+    if (n < 2)
+        return 0;
+    uint64_t *keys = malloc(n * sizeof *keys);
+    if (!keys)
+        return UINT64_MAX;
+    orc_enumerate(c, t0, t1, keys, n);
+    qsort(keys, n, sizeof *keys, orc_cmp_u64);
+    uint64_t dup = 0;
+    for (uint64_t i = 1; i < n; i++)
+        if (keys[i] == keys[i - 1])
+            dup++;
+    free(keys);
+    return dup;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Host-threaded model of the lockless operations on packed slots           */
+/* ------------------------------------------------------------------------ */
+/*
+ * Algorithm 1 (iceberg find-or-put) and Algorithm 4 (cuckoo put) run by many
+ * POSIX threads at once on one table. Section 4.5 observes that atomic
+ * instructions are too coarse for small slots; here, as in the GPU kernels,
+ * a slot is one field of a 64-bit word and a claim is a compare-and-swap of
+ * the whole word that succeeds only if the target field is still EMPTY:
+ *   - a snapshot reads a bucket word by word (each word atomically, the
+ *     bucket as a whole possibly torn);
+ *   - the claim index is the number of filled fields in the snapshot, which
+ *     is never past the true first empty slot because fields only ever go
+ *     from EMPTY to filled (Section 3, Limitations: filled slots form a
+ *     prefix);
+ *   - a failed compare-and-swap whose target field is still EMPTY (only a
+ *     neighbouring field changed) is retried with the word it returned, at
+ *     most 64 times; otherwise the field's new value decides: the key's own
+ *     entry means another thread put it (FOUND), anything else means the
+ *     bucket is read again;
+ *   - a cuckoo swap is a compare-and-swap loop that exchanges one field.
+ * Each retry loop has a bound; a key that exhausts it gets status 5 (error).
+ * This is test infrastructure: it pins the packed-word claim protocol on the
+ * CPU (no duplicate keys, one PUT per distinct key, conservation of keys),
+ * and it shares no code with the CUDA library.
+ */
+#include <pthread.h>
+#include <sched.h>
+
+#define ORC_ERROR 5
+
+static uint64_t mt_load(const uint64_t *p)
+{
+    return __atomic_load_n(p, __ATOMIC_RELAXED);
+}
+
+/* the fields of bucket a, read word by word; returns the number of filled
+ * fields and sets *hit if one equals e */
+static int mt_snapshot(const orc_cfg *c, int level, const uint64_t *table,
+                       uint64_t a, uint64_t e, uint64_t *words, int *hit)
+{
+    int fpw = c->fpw[level], s = 64 / fpw, filled = 0;
+    *hit = 0;
+    for (int w = 0; w < c->wpb; w++) {
+        words[w] = mt_load(&table[a * (uint64_t)c->wpb + (uint64_t)w]);
+        for (int f = 0; f < fpw; f++) {
+            uint64_t v = (words[w] >> (f * s)) & orc_low_mask(s);
+            filled += v != 0;
+            *hit |= v == e;
+        }
+    }
+    return filled;
+}
+
+/* EMPTY -> e on field f of *wp; snap is the word as the snapshot saw it.
+ * 1 if written; otherwise *seen is the value that won the field (0 if the
+ * bounded retry gave up and the bucket has to be read again). */
+static int mt_claim(uint64_t *wp, int f, int fpw, uint64_t snap, uint64_t e,
+                    uint64_t *seen, uint64_t *fails)
+{
+    int s = 64 / fpw;
+    uint64_t m = orc_low_mask(s) << (f * s);
+    uint64_t expected = snap & ~m;
+    for (int it = 0; it < 64; it++) {
+        uint64_t old = expected;
+        uint64_t desired = expected | (e << (f * s));
+        if (__atomic_compare_exchange_n(wp, &old, desired, 0, __ATOMIC_RELAXED,
+                                        __ATOMIC_RELAXED))
+            return 1;
+        (*fails)++;
+        uint64_t fld = (old & m) >> (f * s);
+        if (fld != 0) {
+            *seen = fld;
+            return 0;
+        }
+        expected = old; /* only a neighbouring field changed */
+    }
+    *seen = 0;
+    return 0;
+}
+
+/* exchange field f of *wp with e; 1 and *prev = the old field on success,
+ * 0 if the bounded retry gave up */
+static int mt_swap(uint64_t *wp, int f, int fpw, uint64_t snap, uint64_t e,
+                   uint64_t *prev)
+{
+    int s = 64 / fpw;
+    uint64_t m = orc_low_mask(s) << (f * s);
+    uint64_t expected = snap;
+    for (int it = 0; it < 4096; it++) {
+        uint64_t old = expected;
+        uint64_t desired = (expected & ~m) | (e << (f * s));
+        if (__atomic_compare_exchange_n(wp, &old, desired, 0, __ATOMIC_RELAXED,
+                                        __ATOMIC_RELAXED)) {
+            *prev = (expected & m) >> (f * s);
+            return 1;
+        }
+        expected = old;
+    }
+    return 0;
+}
+
+static uint64_t *mt_word(const orc_cfg *c, int level, uint64_t *table,
+                         uint64_t a, int y)
+{
+    return &table[a * (uint64_t)c->wpb + (uint64_t)(y / c->fpw[level])];
+}
+
+/* Algorithm 1 for one key, with the claims above */
+static int mt_iceberg_fop1(const orc_cfg *c, uint64_t *t0, uint64_t *t1,
+                           uint64_t k, uint64_t *fails)
+{
+    int B0 = orc_slots_per_bucket(c, 0), B1 = orc_slots_per_bucket(c, 1);
+    int max_iter = 4 * (B0 + 2 * B1) + 16;
+    uint64_t w0[16], w1[16], w2[16];
+    uint64_t a0 = orc_iceberg_bucket(c, 0, k), e0 = orc_iceberg_entry(c, 0, k);
+    int it = 0, hit;
+    /* level 1: the primary bucket */
+    for (;;) {
+        if (++it > max_iter)
+            return ORC_ERROR;
+        int y = mt_snapshot(c, 0, t0, a0, e0, w0, &hit);
+        if (hit)
+            return ORC_FOUND;
+        if (y == B0)
+            break;
+        uint64_t seen = 0;
+        int fpw = c->fpw[0];
+        if (mt_claim(mt_word(c, 0, t0, a0, y), y % fpw, fpw, w0[y / fpw], e0,
+                     &seen, fails))
+            return ORC_PUT;
+        if (seen == e0)
+            return ORC_FOUND;
+    }
+    /* level 2: both secondary buckets, the less full one (ties to the
+     * second: Definition 1) */
+    uint64_t a1 = orc_iceberg_bucket(c, 1, k), e1 = orc_iceberg_entry(c, 1, k);
+    uint64_t a2 = orc_iceberg_bucket(c, 2, k), e2 = orc_iceberg_entry(c, 2, k);
+    for (;;) {
+        if (++it > max_iter)
+            return ORC_ERROR;
+        int h1, h2;
+        int y1 = mt_snapshot(c, 1, t1, a1, e1, w1, &h1);
+        int y2 = mt_snapshot(c, 1, t1, a2, e2, w2, &h2);
+        if (h1 || h2)
+            return ORC_FOUND;
+        int pick1 = y1 < y2;
+        int y = pick1 ? y1 : y2;
+        if (y == B1)
+            return ORC_FULL;
+        uint64_t a = pick1 ? a1 : a2, e = pick1 ? e1 : e2;
+        uint64_t *snap = pick1 ? w1 : w2;
+        uint64_t seen = 0;
+        int fpw = c->fpw[1];
+        if (mt_claim(mt_word(c, 1, t1, a, y), y % fpw, fpw, snap[y / fpw], e,
+                     &seen, fails))
+            return ORC_PUT;
+        if (seen == e)
+            return ORC_FOUND;
+    }
+}
+
+/* Algorithm 4 for one key: a lost claim, like a swap, uses up a step */
+static int mt_cuckoo_put(const orc_cfg *c, uint64_t *table, uint64_t k,
+                         uint64_t *dropped, uint64_t *fails)
+{
+    int B = orc_slots_per_bucket(c, 0), fpw = c->fpw[0];
+    uint64_t w[16];
+    int j = 0, hit;
+    for (int step = 1; step <= c->max_chain; step++) {
+        uint64_t a = orc_address(c, 0, j, k);
+        uint64_t e = orc_cuckoo_entry(c, j, k);
+        int y = mt_snapshot(c, 0, table, a, e, w, &hit);
+        if (y < B) {
+            uint64_t seen = 0;
+            if (mt_claim(mt_word(c, 0, table, a, y), y % fpw, fpw, w[y / fpw],
+                         e, &seen, fails))
+                return ORC_PUT;
+            continue;
+        }
+        int ys = (int)orc_evict_slot(k, step, B);
+        uint64_t prev = 0;
+        if (!mt_swap(mt_word(c, 0, table, a, ys), ys % fpw, fpw, w[ys / fpw], e,
+                     &prev))
+            return ORC_ERROR;
+        if (prev == 0)
+            return ORC_PUT; /* the chosen slot held nothing */
+        int jo;
+        k = orc_cuckoo_decode(c, a, prev, &jo);
+        j = (jo + 1) % c->num_hashes;
+    }
+    *dropped = k;
+    return ORC_FULL;
+}
+
+typedef struct {
+    const orc_cfg *c;
+    uint64_t *t0, *t1;
+    const uint64_t *keys;
+    size_t n;
+    uint8_t *status;
+    uint64_t *dropped;
+    int tid, nthreads;
+    const int *go;
+    uint64_t fails;
+} mt_job;
+
+static void *mt_worker(void *arg)
+{
+    mt_job *j = arg;
+    while (!__atomic_load_n(j->go, __ATOMIC_ACQUIRE))
+        sched_yield(); /* start together */
+    /* thread t takes keys t, t + T, t + 2T, ...: copies of one key, and keys
+     * of one bucket, land on different threads */
+    for (size_t i = (size_t)j->tid; i < j->n; i += (size_t)j->nthreads) {
+        uint64_t k = j->keys[i], d = 0;
+        if (!orc_valid_key(j->c, k)) {
+            j->status[i] = ORC_INVALID;
+            continue;
+        }
+        if (j->c->kind == 1) {
+            j->status[i] = (uint8_t)mt_iceberg_fop1(j->c, j->t0, j->t1, k, &j->fails);
+        } else {
+            j->status[i] = (uint8_t)mt_cuckoo_put(j->c, j->t0, k, &d, &j->fails);
+            if (j->dropped)
+                j->dropped[i] = d;
+        }
+    }
+    return NULL;
+}
+
+/* Run the operation of the table's kind (iceberg find-or-put, cuckoo put)
+ * on nthreads threads at once. Returns the number of threads that ran
+ * concurrently (if some could not be started, their shares of the keys run
+ * afterwards on the calling thread), or -1 on bad arguments. *fails_out (may
+ * be NULL) counts compare-and-swaps that lost. */
+int orc_concurrent_insert(const orc_cfg *c, uint64_t *t0, uint64_t *t1,
+                          const uint64_t *keys, size_t n, uint8_t *status,
+                          uint64_t *dropped, int nthreads, uint64_t *fails_out)
+{
+    if (nthreads < 1 || nthreads > 256 || c->wpb > 16)
+        return -1;
+    pthread_t th[256];
+    int ok[256] = {0};
+    mt_job jobs[256];
+    int go = 0;
+    for (int t = 0; t < nthreads; t++) {
+        mt_job jb = {c, t0, t1, keys, n, status, dropped, t, nthreads, &go, 0};
+        jobs[t] = jb;
+    }
+    int running = 1;
+    for (int t = 1; t < nthreads; t++) {
+        ok[t] = pthread_create(&th[t], NULL, mt_worker, &jobs[t]) == 0;
+        running += ok[t];
+    }
+    __atomic_store_n(&go, 1, __ATOMIC_RELEASE);
+    mt_worker(&jobs[0]);
+    uint64_t fails = jobs[0].fails;
+    for (int t = 1; t < nthreads; t++) {
+        if (ok[t])
+            pthread_join(th[t], NULL);
+        else
+            mt_worker(&jobs[t]);
+        fails += jobs[t].fails;
+    }
+    if (fails_out)
+        *fails_out = fails;
+    return running;
 }

@@ -72,6 +72,14 @@ uint64_t orc_table_words(const orc_cfg *c, int level);
 int orc_slots_per_bucket(const orc_cfg *c, int level);
 uint64_t orc_get_slot(const orc_cfg *c, int level, const uint64_t *table,
                       uint64_t bucket, int y);
+/* write slot y of a bucket (tests use it to plant invariant violations) */
+void orc_set_slot(const orc_cfg *c, int level, uint64_t *table,
+                  uint64_t bucket, int y, uint64_t v);
+/* the encoded entry of key k under choice x, and the bucket it belongs in:
+ * cuckoo x = hash index j (level 0); iceberg x = 0 primary, 1 and 2 the two
+ * secondary choices (level 1) */
+uint64_t orc_entry_of(const orc_cfg *c, int x, uint64_t k);
+uint64_t orc_bucket_of(const orc_cfg *c, int x, uint64_t k);
 
 /* --- operations (all sequential, keys in input order) --- */
 /* Algorithm 4 read sequentially. status[i] in {PUT, FULL, INVALID}; when a put
@@ -118,6 +126,21 @@ uint64_t orc_check_order_property(const orc_cfg *c, const uint64_t *t0,
                                   const uint64_t *t1);
 /* cuckoo: an entry stored under hash index j has buckets a_0..a_{j-1} full */
 uint64_t orc_check_cuckoo_chain(const orc_cfg *c, const uint64_t *table);
+/* stored entries minus distinct stored keys (0 when no key is held twice) */
+uint64_t orc_check_duplicates(const orc_cfg *c, const uint64_t *t0,
+                              const uint64_t *t1);
+
+/* --- host-threaded model of the lockless operations on packed slots ---
+ * The table kind's write operation (iceberg: Algorithm 1 find-or-put; cuckoo:
+ * Algorithm 4 put) run by nthreads POSIX threads at once, thread t taking
+ * keys t, t + nthreads, ...; every claim is a compare-and-swap of one field
+ * of a 64-bit word, retried while only neighbouring fields changed. status
+ * as for the sequential operations, plus 5 when a bounded retry loop gave
+ * up. Returns the number of threads that ran concurrently, -1 on bad
+ * arguments; *fails_out (may be NULL) counts lost compare-and-swaps. */
+int orc_concurrent_insert(const orc_cfg *c, uint64_t *t0, uint64_t *t1,
+                          const uint64_t *keys, size_t n, uint8_t *status,
+                          uint64_t *dropped, int nthreads, uint64_t *fails_out);
 
 #ifdef __cplusplus
 }

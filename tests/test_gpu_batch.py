@@ -76,6 +76,7 @@ def check_table(t, k, st):
     assert np.array_equal(np.sort(u64(stored)), np.sort(o.enumerate()))
     d = dump(t)
     assert d.check_entries() == 0 and d.check_order_property() == 0 and d.check_prefix() == 0
+    assert d.check_duplicates() == 0
 
 
 @pytest.mark.parametrize("tile,items", [(4, 2), (8, 1), (16, 8)])

@@ -177,6 +177,7 @@ def test_cuckoo_2e14_fill_08_lookup_parity(T, items, P):
     assert d.probes == gprobes
     assert d.check_prefix() == 0
     assert d.check_entries() == 0
+    assert d.check_duplicates() == 0
     assert d.check_cuckoo_chain() == 0
 
 
@@ -199,6 +200,7 @@ def test_cuckoo_past_capacity_conserves_keys(compact, P):
     assert np.array_equal(both, np.sort(keys.numpy().astype(np.uint64)))
     d = dump_into(mirror(t), t)
     assert d.check_prefix() == 0 and d.check_entries() == 0 and d.check_cuckoo_chain() == 0
+    assert d.check_duplicates() == 0
     # lookups are exact membership
     stored_set = set(u64(stored).tolist())
     got = t.find(keys.to(DEV)).cpu().numpy() == cht().FOUND
@@ -220,6 +222,7 @@ def test_cuckoo_noncompact_equal_slots_fastrange():
     d = dump_into(mirror(t), t)
     assert (d.find(q.numpy().astype(np.uint64)) == got).all()
     assert d.check_entries() == 0 and d.check_cuckoo_chain() == 0
+    assert d.check_duplicates() == 0
 
 
 # --------------------------------------------------------------------------
@@ -237,6 +240,7 @@ def _fop_contract(t, keys_np, st, o_stored):
     assert np.array_equal(np.sort(u64(stored)), np.sort(o_stored))
     d = dump_into(mirror(t), t)
     assert d.check_entries() == 0
+    assert d.check_duplicates() == 0
     assert d.check_order_property() == 0
     assert d.check_prefix() == 0
     return d
@@ -298,6 +302,7 @@ def test_iceberg_past_capacity_theorem1(compact):
     assert len(np.unique(s)) == len(s), "no duplicates (Lemma, Appendix A)"
     d = dump_into(mirror(t), t)
     assert d.check_entries() == 0 and d.check_order_property() == 0 and d.check_prefix() == 0
+    assert d.check_duplicates() == 0
     stored_set = set(s.tolist())
     # (c) found/put iff present afterwards; (d) one put per stored key
     present = np.array([int(k) in stored_set for k in kn])
@@ -473,6 +478,7 @@ def test_iceberg_2e22_full_size_stream():
     del stored, keys, is_find
     d = dump_into(mirror(t), t)
     assert d.check_entries() == 0 and d.check_order_property() == 0 and d.check_prefix() == 0
+    assert d.check_duplicates() == 0
     g = torch.Generator(device=DEV)
     g.manual_seed(1)
     sample = torch.cat([seen[torch.randint(0, seen.numel(), (100000,), device=DEV, generator=g)],

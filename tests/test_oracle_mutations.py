@@ -1,6 +1,7 @@
 """The oracle's pins must catch plausible mistakes. Each case plants one
 mistake in a scratch copy of the oracle's C source (on the CPU: a dropped
-term, a wrong sign, index or tag, a flipped comparison), rebuilds the copy
+term, a wrong sign, index or tag, a flipped comparison, in the algorithms
+and in the invariant checkers), rebuilds the copy
 and runs the oracle pin tests against it in a subprocess; at least one pin
 must fail. An unmutated copy must pass, so a failure means the mistake, not
 the harness."""
@@ -21,7 +22,8 @@ MUTATIONS = [
     ("inverse permutation drops the round function",
      "uint64_t L = (p >> R) ^ orc_round(c, level, j, r);", "uint64_t L = (p >> R);"),
     ("evicted key continues under the wrong hash",
-     "j = (jo + 1) % c->num_hashes;", "j = (j + 1) % c->num_hashes;"),
+     "k = orc_cuckoo_decode(c, a, old, &jo);\n        j = (jo + 1) % c->num_hashes;",
+     "k = orc_cuckoo_decode(c, a, old, &jo);\n        j = (j + 1) % c->num_hashes;"),
     ("Algorithm 5 ignores the slot order",
      "if (bx < 0 || orc_prec(x, y, bx, by)) {", "if (bx < 0) {"),
     ("round function shifted by one bit",
@@ -40,6 +42,45 @@ MUTATIONS = [
     ("enumeration decodes primary entries without the flag shift",
      "return c->compact ? orc_key_from(c, 0, 0, a, e >> 1) : e >> 1;",
      "return c->compact ? orc_key_from(c, 0, 0, a, e >> 2) : e >> 1;"),
+    # mistakes in the invariant checkers themselves
+    ("prefix checker counts every late slot, not every bucket",
+     "else if (seen_empty) {\n                bad++;\n                break;",
+     "else if (seen_empty) {\n                bad++;"),
+    ("order-property checker with the slot order reversed",
+     "if (!orc_prec(x2, y2, x, y))", "if (!orc_prec(x, y, x2, y2))"),
+    ("order-property checker never visits the secondary level",
+     "for (int level = 0; level < 2; level++) {", "for (int level = 0; level < 1; level++) {"),
+    ("order-property checker misses a preceding copy of the same key",
+     "if (e2 == 0 || e2 == orc_iceberg_entry(c, x2, k)) {", "if (e2 == 0) {"),
+    ("order-property checker looks in the wrong bucket",
+     "orc_iceberg_bucket(c, x2, k), y2);", "orc_iceberg_bucket(c, x, k), y2);"),
+    ("chain checker also inspects the entry's own bucket",
+     "for (int jj = 0; jj < j; jj++)", "for (int jj = 0; jj <= j; jj++)"),
+    ("chain checker skips the first bucket of the chain",
+     "for (int jj = 0; jj < j; jj++)", "for (int jj = 1; jj < j; jj++)"),
+    ("entries checker accepts a hash index equal to H",
+     "ok = x >= 0 && x < c->num_hashes &&", "ok = x >= 0 && x <= c->num_hashes &&"),
+    ("entries checker skips the cuckoo address test",
+     "orc_address(c, 0, x, k) == a &&", ""),
+    ("entries checker skips the secondary address test",
+     "orc_iceberg_bucket(c, x, k) == a &&", ""),
+    # mistakes in the host-threaded model of the packed-word claim
+    ("threaded claim writes the word without a compare-and-swap",
+     "        if (__atomic_compare_exchange_n(wp, &old, desired, 0, __ATOMIC_RELAXED,\n"
+     "                                        __ATOMIC_RELAXED))\n            return 1;\n"
+     "        (*fails)++;",
+     "        __atomic_store_n(wp, desired, __ATOMIC_RELAXED);\n        return 1;\n"
+     "        (*fails)++;"),
+    ("threaded put continues the evicted key under the wrong hash",
+     "k = orc_cuckoo_decode(c, a, prev, &jo);\n        j = (jo + 1) % c->num_hashes;",
+     "k = orc_cuckoo_decode(c, a, prev, &jo);\n        j = (j + 1) % c->num_hashes;"),
+    ("threaded level-2 choice gives ties to the first bucket",
+     "int pick1 = y1 < y2;", "int pick1 = y1 <= y2;"),
+    ("threaded claim takes a lost field as its own",
+     "        if (fld != 0) {\n            *seen = fld;", "        if (fld != 0) {\n            *seen = e;"),
+    ("duplicates checker skips the first pair",
+     "for (uint64_t i = 1; i < n; i++)\n        if (keys[i] == keys[i - 1])",
+     "for (uint64_t i = 2; i < n; i++)\n        if (keys[i] == keys[i - 1])"),
 ]
 
 
