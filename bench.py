@@ -404,18 +404,47 @@ def run_e2e(wl, steps, warmup, direct=False):
 # ---------------------------------------------------------------------------
 # the oracle, timed on the host cores (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
+def cuckoo_geometry(spec):
+    """Fields per word, hash count and chain bound of the benchmark's cuckoo
+    table, worked out here rather than through the GPU library (the CPU legs
+    load only the oracle): whole-key tables hold one 64-bit slot per word;
+    compact ones the densest packing that fits w - log2(buckets) remainder
+    bits plus two hash-index bits; H = 3, C = 128."""
+    w, nb = spec["key_bits"], spec["num_buckets"]
+    if not spec["compact"]:
+        return 1, 3, 128
+    need = w - (nb - 1).bit_length() + 2
+    fpw = max(f for f in (1, 2, 3, 4) if need <= 64 // f)
+    return fpw, 3, 128
+
+
+def host_cpu_model() -> str:
+    """CPU model of the host the oracle runs on (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def oracle_sample(spec, n_ins, n_find, seed_index=None):
     import oracle
     from paper_2406_09255_gb300 import workloads as W
     seed = W.SEED_BASE + spec["seed_index"]
     w = spec["key_bits"]
-    # geometry as the GPU table resolves it
-    from paper_2406_09255_gb300 import resolve_config
-    c = resolve_config(spec["kind"], w, spec["num_buckets"], compact=spec["compact"],
-                       key_bytes=spec["key_bytes"], seed=1000 * spec["seed_index"])
-    o = oracle.Table(oracle.CUCKOO, w, c.num_buckets, compact=bool(c.compact),
-                     fpw0=c.fields_per_word, num_hashes=c.num_hashes, max_chain=c.max_chain,
-                     seed=c.seed)
+    fpw, H, C = cuckoo_geometry(spec)
+    o = oracle.Table(oracle.CUCKOO, w, spec["num_buckets"], compact=bool(spec["compact"]),
+                     fpw0=fpw, num_hashes=H, max_chain=C, seed=1000 * spec["seed_index"])
     keys = W.unique_keys(0, n_ins, w, seed).numpy().astype(np.uint64)
     # lookups: the inserted keys and as many absent ones, shuffled, repeated
     # cyclically up to n_find queries (50 % hit)
@@ -437,7 +466,7 @@ def cpu_baseline(spec, budget_s=25.0):
     n_find = total - n_ins
     rate, dt = oracle_sample(spec, n_ins, n_find)
     return {"value": rate, "unit": "Mops/s", "cores": 1, "kind": "oracle",
-            "seconds": dt,
+            "seconds": dt, "cpu_model": host_cpu_model(), "nproc": os.cpu_count(),
             "sample": (f"sequential C oracle on the full {spec['num_buckets']}-bucket table: "
                        f"{n_ins} inserts of the workload's key sequence then {n_find} lookups "
                        f"at 50% hit (insert:lookup = 2:13 as in the step), one thread")}
@@ -466,6 +495,7 @@ def reference_arm(args, spec, name):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": describe(name, spec, 805306368 if spec["compact"] else 0)},
         "cpu_baseline": {"value": value, "unit": "Mops/s", "cores": 1, "kind": "oracle",
+                         "cpu_model": host_cpu_model(), "nproc": os.cpu_count(),
                          "sample": f"per step {n_ins} inserts + {per_step - n_ins} lookups at "
                                    f"50% hit on the full-size table, sequential C oracle"},
         "e2e": {"value": value, "unit": "Mops/s", "h2d_bytes_per_step": 0,

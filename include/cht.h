@@ -112,6 +112,14 @@ typedef struct cht_table cht_table; /* opaque host handle */
  *                       lanes take the next key (a stream of fully packed
  *                       rounds). Lookup answers and probe counts are the
  *                       same for every value. Iceberg operations ignore it.
+ * retry_limit           iceberg find-or-put: lost claims a key may retry
+ *                       before it gives up with status CHT_ERROR, 0..32767
+ *                       (0 = the built-in bound, which a correct run never
+ *                       reaches: a key can lose at most once per slot of
+ *                       its three buckets, Appendix A). A small value lets a
+ *                       test drive the error path (CHT_ERROR statuses and
+ *                       cht_error_flags) under contention; set it at
+ *                       cht_create. Cuckoo tables ignore it.
  */
 typedef struct cht_config {
     int32_t kind;
@@ -131,7 +139,8 @@ typedef struct cht_config {
     int32_t max_ctas;
     int32_t max_tiles;
     int32_t lookups_in_flight;
-    int32_t reserved[2];
+    int32_t retry_limit;
+    int32_t reserved;
 } cht_config;
 
 /* Device counters a table can accumulate into (see cht_set_counters). */
@@ -270,6 +279,15 @@ int cht_values_gather(const uint64_t *d_slots, size_t n, const void *d_store, in
  * (CHT_ERR_UNSUPPORTED otherwise); values aligned to value_bytes
  * (CHT_ERR_INVALID otherwise); keys, statuses and errors as for
  * cht_find_or_put / cht_find.
+ * Ordering: a value is written by a plain store after its key's slot has
+ * been claimed, and nothing orders the two for other threads. So a
+ * cht_kv_get that runs concurrently with a cht_kv_put of the same key (other
+ * streams) may find the key and read the slot's previous value (zero for a
+ * fresh slot); order them on one stream for the new value. A 16-byte value
+ * is written as one 16-byte store, whose two 8-byte halves are separate
+ * single-copy atomic accesses: when a key is given twice in one cht_kv_put,
+ * each half of the stored value comes from one of the copies, not
+ * necessarily the same one. 4- and 8-byte values are written whole.
  */
 int cht_kv_put(cht_table *t, const void *d_keys, size_t n, const void *d_values, int value_bytes,
                void *d_store, uint64_t store_slots, uint8_t *d_status, void *stream);
@@ -371,17 +389,20 @@ int cht_batch_destroy(cht_batch *b);
  *
  * The batch descriptors live in a fixed array inside the library (device
  * memory that every GPU which loads the library holds until the process
- * exits) with room for CHT_STATIC_BATCH_MAX tables; count above that is
- * rejected with CHT_ERR_INVALID. Nothing is allocated on any call: the
- * descriptors are written into the array by a copy on stream, then the fused
- * kernel runs. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call shares the one array and each call
- * overwrites the descriptors it uses (nothing in it has to start at zero), so
- * calls whose work overlaps on the GPU (different streams, or different host
- * threads) race: order them on one stream. Arguments and per-key results are
- * as for cht_batch_create / cht_find_or_put; all tables must be iceberg tables
- * with the same primary packing on the current device.
+ * exits) with room for CHT_STATIC_BATCH_MAX tables (224 bytes each, 56 KiB in
+ * all); count above that is rejected with CHT_ERR_INVALID. Nothing is
+ * allocated on any call: the descriptors travel to the array as the
+ * parameters of small kernel launches on stream (so the host never waits),
+ * then the fused kernel runs. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current, and looks
+ * it up again if the device's context has changed since (cudaDeviceReset);
+ * make that first call before any stream capture. Every call shares the one
+ * array and each call overwrites the descriptors it uses (nothing in it has
+ * to start at zero), so calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race: order them on one stream.
+ * Arguments and per-key results are as for cht_batch_create /
+ * cht_find_or_put; all tables must be iceberg tables with the same primary
+ * packing on the current device.
  */
 #define CHT_STATIC_BATCH_MAX 256
 int cht_batch_find_or_put_static(cht_table *const *tables, const void *const *d_keys,

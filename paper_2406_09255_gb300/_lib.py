@@ -39,7 +39,8 @@ class Config(ctypes.Structure):
         ("max_ctas", ctypes.c_int32),
         ("max_tiles", ctypes.c_int32),
         ("lookups_in_flight", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("retry_limit", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

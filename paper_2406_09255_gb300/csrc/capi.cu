@@ -135,6 +135,8 @@ int resolve(const cht_config *in, cht_config *out) {
         return fail(CHT_ERR_INVALID, "cta_threads must be a multiple of 32 in [32, 256]");
     if (c.max_ctas < 0 || c.max_tiles < 0)
         return fail(CHT_ERR_INVALID, "max_ctas and max_tiles must be >= 0");
+    if (c.retry_limit < 0 || c.retry_limit > 32767)
+        return fail(CHT_ERR_INVALID, "retry_limit must be 0..32767");
     if (c.lookups_in_flight == 0) c.lookups_in_flight = 4;
     if (c.lookups_in_flight != 1 && c.lookups_in_flight != 4 && c.lookups_in_flight != 8)
         return fail(CHT_ERR_INVALID, "lookups_in_flight must be 1, 4 or 8");
@@ -260,7 +262,8 @@ int cht_create(const cht_config *cfg, void *d_mem, size_t bytes, void *stream, c
     a.key_bytes = c.key_bytes;
     a.H = c.num_hashes;
     a.C = c.max_chain;
-    a.compact = c.compact;
+    a.compact = (int16_t)c.compact;
+    a.retry_limit = (int16_t)c.retry_limit;
     a.max_tiles = c.max_tiles;
     a.err = reinterpret_cast<uint32_t *>(t->mem);
     a.ctr = nullptr;
@@ -728,26 +731,69 @@ int cht_batch_destroy(cht_batch *b) {
 // ---------------------------------------------------------------------------
 namespace {
 
+// the descriptor layout the documented limit is stated in (256 x 224 bytes)
+static_assert(sizeof(BatchDesc) == 224, "batch descriptor size changed: update cht.h");
+
 // room for CHT_STATIC_BATCH_MAX descriptors; held by every GPU that loads the
 // library until the process exits
 static __device__ __align__(256) unsigned char
     g_static_batch[CHT_STATIC_BATCH_MAX * sizeof(BatchDesc)];
 
+// Driver calls that identify the current context, looked up through the
+// runtime so that the library needs no link-time dependency on the driver.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-void *g_static_addr[kMaxDevices];  // device address of g_static_batch, per device
+struct StaticAddr {
+    unsigned long long ctx;  // id of the context the address belongs to (0: none)
+    void *addr;
+};
+StaticAddr g_static_addr[kMaxDevices];
 
-// the array's device address on device dev (current): looked up on the first
-// call on that device, then reused
+// id of the current context, or 0 if there is none or it cannot be read
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0)
+        return 0;
+    return id;
+}
+
+// The array's device address on device dev (current). It is looked up with
+// cudaGetSymbolAddress on the first call on the device and again whenever the
+// device's context has changed since (after cudaDeviceReset the module is
+// loaded anew and the array may move); otherwise the cached address is used.
 int static_batch_address(int dev, void **out) {
     std::lock_guard<std::mutex> g(g_static_mu);
-    if (!g_static_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    StaticAddr &c = g_static_addr[dev];
+    if (!c.addr || ctx == 0 || c.ctx != ctx) {
         void *p = nullptr;
         cudaError_t ce = cudaGetSymbolAddress(&p, g_static_batch);
         if (ce != cudaSuccess) return cuda_fail(ce, "looking up the static batch array");
-        g_static_addr[dev] = p;
+        c.addr = p;
+        // the lookup made the primary context current if it was not yet
+        c.ctx = ctx ? ctx : current_context_id();
     }
-    *out = g_static_addr[dev];
+    *out = c.addr;
     return CHT_OK;
 }
 
@@ -766,8 +812,6 @@ extern "C" int cht_batch_find_or_put_static(cht_table *const *tables, const void
     cudaError_t ce = cudaGetDevice(&cur);
     if (ce != cudaSuccess) return cuda_fail(ce, "device query");
     if (cur < 0 || cur >= kMaxDevices) return fail(CHT_ERR_UNSUPPORTED, "device id %d", cur);
-    // descriptors are built on the stack (80 KB at most): no allocation
-    BatchDesc host[CHT_STATIC_BATCH_MAX];
     int fpw0 = 0, sms = 0;
     uint64_t total_chunks = 0;
     const uint64_t per = (uint64_t)32 * kStaticBatchItems;
@@ -788,24 +832,34 @@ extern "C" int cht_batch_find_or_put_static(cht_table *const *tables, const void
             return fail(CHT_ERR_INVALID, "null keys or statuses at batch entry %d", i);
         if ((uintptr_t)d_keys[i] % t->cfg.key_bytes)
             return fail(CHT_ERR_INVALID, "keys of batch entry %d not aligned", i);
-        host[i].ta = t->args;
-        host[i].ta.max_tiles = 0;
-        host[i].ta.ctr = nullptr;
-        host[i].keys = d_keys[i];
-        host[i].n = n[i];
-        host[i].status = d_status[i];
         total_chunks += (n[i] + per - 1) / per;
     }
     void *dst = nullptr;
     int e = static_batch_address(cur, &dst);
     if (e) return e;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // a copy from pageable memory returns once the source has been consumed,
-    // so the stack copy may go out of scope right after
-    ce = cudaMemcpyAsync(dst, host, sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "writing the static batch descriptors");
+    BatchDesc *dev_desc = static_cast<BatchDesc *>(dst);
+    // descriptors travel as kernel parameters, kDescPerLaunch per launch (a
+    // block of 64 x 224 bytes = 14 KiB on the stack), as in cht_batch_create:
+    // the upload is an ordinary asynchronous launch on stream
+    for (int i0 = 0; i0 < count; i0 += kDescPerLaunch) {
+        const int m = std::min(kDescPerLaunch, count - i0);
+        DescBlock blk;
+        for (int i = 0; i < m; ++i) {
+            const cht_table *t = tables[i0 + i];
+            BatchDesc &d = blk.d[i];
+            d.ta = t->args;
+            d.ta.max_tiles = 0;
+            d.ta.ctr = nullptr;
+            d.keys = d_keys[i0 + i];
+            d.n = n[i0 + i];
+            d.status = d_status[i0 + i];
+        }
+        k_write_desc<<<1, 128, 0, s>>>(dev_desc + i0, blk, m);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) return cuda_fail(ce, "writing the static batch descriptors");
+    }
     if (total_chunks == 0) return ok();
-    ce = launch_iceberg_batch_noalloc(fpw0, s, sms, static_cast<const BatchDesc *>(dst), count,
-                                      total_chunks);
+    ce = launch_iceberg_batch_noalloc(fpw0, s, sms, dev_desc, count, total_chunks);
     return ce == cudaSuccess ? ok() : cuda_fail(ce, "static batch kernel launch");
 }

@@ -43,18 +43,29 @@ struct Level {
     uint64_t B[3];    // Feistel round-function offsets, per hash
 };
 
-// Everything a kernel needs about a table, passed by value.
+// Everything a kernel needs about a table, passed by value (200 bytes; a
+// batch descriptor of the fused launch embeds it).
 struct TableArgs {
     Level lv[2];
     int w;                    // key bits
     int key_bytes;            // 4 or 8
     int H;                    // cuckoo hash count
     int C;                    // cuckoo chain bound
-    int compact;              // 1: remainders, 0: whole keys
+    int16_t compact;          // 1: remainders, 0: whole keys
+    int16_t retry_limit;      // iceberg: lost claims a key may retry (0 = built-in bound)
     int max_tiles;            // 0 = unbounded
     uint32_t *err;            // header error word
     unsigned long long *ctr;  // optional cht_counters (probes, writes, cas_fail, ops)
 };
+
+// Lost claims an iceberg find-or-put may retry before it reports ST_ERROR.
+// Every lost claim means another key filled a slot of the same buckets, and
+// fields are never emptied, so a key can lose at most once per slot of its
+// three buckets (Appendix A, termination); the bound adds a margin to that.
+// A table configured with retry_limit > 0 uses that instead.
+__host__ __device__ __forceinline__ int iceberg_retry_bound(const TableArgs &ta, int B0, int B1) {
+    return ta.retry_limit > 0 ? ta.retry_limit : 4 * (B0 + 2 * B1) + 16;
+}
 
 // ---------------------------------------------------------------------------
 // splitmix64 (Steele, Lea and Flood 2014)

@@ -546,7 +546,7 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
                     n_write++;
                 } else {
                     const uint64_t mine = (lvl == 1) ? e0 : (pick_a ? ea : eb);
-                    const int max_iter = 4 * (kWordsPerBucket * FPW0 + 2 * B1) + 16;
+                    const int max_iter = iceberg_retry_bound(ta, kWordsPerBucket * FPW0, B1);
                     if (seen == mine) {
                         st = ST_FOUND;  // another thread inserted k first
                     } else if (++it > max_iter) {

@@ -101,7 +101,7 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
         const int FPW1 = L1.fpw;
         const int LF1 = W * FPW1;
         const int B1 = kWordsPerBucket * FPW1;
-        const int max_iter = 4 * (kWordsPerBucket * FPW0 + 2 * B1) + 16;
+        const int max_iter = iceberg_retry_bound(ta, kWordsPerBucket * FPW0, B1);
         const uint64_t *w0 = L0.words + tl * W;
         const uint64_t *w1 = L1.words + tl * W;
 

@@ -27,7 +27,9 @@ class KVMap:
     def put(self, keys: torch.Tensor, values: torch.Tensor, status=None, stream=None):
         """Insert or assign, in one kernel (cht_kv_put). Returns the status
         per key. A key given twice in one call keeps one of its values, which
-        one is unspecified. FULL keys store nothing."""
+        one is unspecified. FULL keys store nothing. A get on another stream
+        that overlaps this put may find a key before its value is written
+        (it then reads the slot's previous value); order them on one stream."""
         if values.dtype != self.values.dtype or values.numel() != keys.numel():
             raise ValueError("one value of the map's dtype per key")
         keys, status = self.table._prep(keys, status)

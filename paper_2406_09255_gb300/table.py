@@ -18,7 +18,7 @@ __all__ = ["Table", "CUCKOO", "ICEBERG", "resolve_config", "table_bytes"]
 def _make_config(kind, key_bits, num_buckets, num_buckets_backyard=0, *, compact=True,
                  key_bytes=8, fields_per_word=0, fields_per_word_backyard=0, num_hashes=0,
                  max_chain=0, seed=0, tile=0, items_per_thread=0, cta_threads=0, max_ctas=0,
-                 max_tiles=0, lookups_in_flight=0) -> Config:
+                 max_tiles=0, lookups_in_flight=0, retry_limit=0) -> Config:
     c = Config()
     c.kind, c.compact, c.key_bits, c.key_bytes = kind, int(compact), key_bits, key_bytes
     c.num_buckets, c.num_buckets_backyard = num_buckets, num_buckets_backyard
@@ -28,6 +28,7 @@ def _make_config(kind, key_bits, num_buckets, num_buckets_backyard=0, *, compact
     c.tile, c.items_per_thread, c.cta_threads = tile, items_per_thread, cta_threads
     c.max_ctas, c.max_tiles = max_ctas, max_tiles
     c.lookups_in_flight = lookups_in_flight
+    c.retry_limit = retry_limit
     return c
 
 

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_binding_struct_matches_header_layout(lib):
-    # 4 ints, 2 u64, 4 ints, u64, 6 ints, 2 reserved ints
+    # 4 ints, 2 u64, 4 ints, u64, 6 ints, retry_limit and one reserved int
     assert ctypes.sizeof(lib.Config) == 4 * 4 + 16 + 4 * 4 + 8 + 6 * 4 + 8
     assert ctypes.sizeof(lib.Counters) == 32
 
@@ -99,6 +99,10 @@ def test_bit_budget_section_5_1(lib):
     (dict(kind=0, key_bits=32, num_buckets=16, lookups_in_flight=2), "lookups_in_flight"),
     (dict(kind=0, key_bits=60, num_buckets=1 << 33), "at most 2^32"),
     (dict(kind=0, key_bits=32, num_buckets=16, lookups_in_flight=16), "lookups_in_flight"),
+    (dict(kind=1, key_bits=32, num_buckets=16, num_buckets_backyard=2, retry_limit=-1),
+     "retry_limit"),
+    (dict(kind=1, key_bits=32, num_buckets=16, num_buckets_backyard=2, retry_limit=40000),
+     "retry_limit"),
 ])
 def test_invalid_configs_rejected_with_message(lib, kw, frag):
     code, _ = _resolve(lib, **kw)

@@ -285,6 +285,37 @@ def test_iceberg_hot_key_contention():
     _fop_contract(t, keys.numpy().astype(np.uint64), st, o.enumerate())
 
 
+def test_bounded_retry_runs_out_and_reports_error():
+    # One primary and one secondary bucket (16 + 16 slots of 64 bits for
+    # 32-bit keys) and 64 distinct keys: in every round the tiles of a warp
+    # race for the same first empty slot and all but one lose. With
+    # retry_limit = 1 a key that loses twice gives up: CHT_ERROR status, the
+    # table's error word set, and the kernel returns normally (no hang, no
+    # trap). The keys that did get an answer follow Algorithm 1.
+    P = cht()
+    keys = W.to_u32(W.unique_keys(0, 64, 32, 9))
+    t = P.Table(P.ICEBERG, 32, 1, 1, key_bytes=4, retry_limit=1, seed=3)
+    st = t.find_or_put(keys.to(DEV)).cpu().numpy()
+    assert (st == P.ERROR).sum() > 0, np.bincount(st)
+    assert ((st == P.ERROR) | (st == P.PUT) | (st == P.FULL)).all()
+    assert t.error_flags() != 0
+    stored, cnt = t.enumerate()
+    kn = u64(keys)
+    assert cnt == (st == P.PUT).sum()
+    assert set(u64(stored).tolist()) == set(kn[st == P.PUT].tolist())
+    d = dump_into(mirror(t), t)
+    assert d.check_entries() == 0 and d.check_order_property() == 0 and d.check_prefix() == 0
+    assert d.check_duplicates() == 0
+    # the error word is cleared with the table; the built-in bound is never
+    # reached on the same race
+    t.clear()
+    assert t.error_flags() == 0
+    t2 = P.Table(P.ICEBERG, 32, 1, 1, key_bytes=4, seed=3)
+    st2 = t2.find_or_put(keys.to(DEV)).cpu().numpy()
+    assert (st2 != P.ERROR).all() and t2.error_flags() == 0
+    assert (st2 == P.PUT).sum() == 32 and (st2 == P.FULL).sum() == 32
+
+
 @pytest.mark.parametrize("compact", [True, False])
 def test_iceberg_past_capacity_theorem1(compact):
     w = 36

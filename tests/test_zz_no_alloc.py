@@ -10,14 +10,19 @@ CHT_STATIC_BATCH_MAX tables) instead of caller scratch.
 
 This file checks, through the C ABI, that the entry point gives the same
 results as the planned batch (cht_batch_create + cht_batch_launch) on two
-calls in a row, and that it rejects batches larger than its array. It is
-collected last so that a failing run has already run every other test.
+calls in a row, that every table's stored set and per-key outcomes equal the
+sequential oracle's replay of its keys (also for a batch of more tables than
+one descriptor upload carries), and that it rejects batches larger than its
+array. It is collected last so that a failing run has already run every other
+test.
 """
 import ctypes
 
 import numpy as np
 import pytest
 import torch
+
+import oracle
 
 from paper_2406_09255_gb300 import workloads as W
 
@@ -62,6 +67,27 @@ def _stored(t):
     return np.sort(out.cpu().numpy().view(np.uint32).astype(np.uint64))
 
 
+def _oracle_replay(t, kn):
+    """The sequential oracle on table t's geometry, fed kn in input order."""
+    c = t.cfg
+    o = oracle.Table(oracle.ICEBERG, c.key_bits, c.num_buckets, c.num_buckets_backyard,
+                     fpw0=c.fields_per_word, fpw1=c.fields_per_word_backyard, seed=c.seed)
+    return o, o.insert(kn)
+
+
+def _check_against_oracle(m, t, kn, st):
+    """Per distinct key the oracle's outcome (one PUT, the rest FOUND, when
+    the replay reports no FULL), and the oracle's stored set."""
+    o, ost = _oracle_replay(t, kn)
+    assert (ost != oracle.FULL).all()
+    uniq, inv = np.unique(kn, return_inverse=True)
+    puts = np.bincount(inv, weights=(st == m.PUT), minlength=len(uniq))
+    oputs = np.bincount(inv, weights=(ost == oracle.PUT), minlength=len(uniq))
+    assert np.array_equal(puts, oputs)
+    assert ((st == m.PUT) | (st == m.FOUND)).all()
+    assert np.array_equal(_stored(t), np.sort(o.enumerate()))
+
+
 def test_static_batch_matches_planned_batch_on_two_calls():
     import paper_2406_09255_gb300 as m
     from paper_2406_09255_gb300.batch import Batch
@@ -91,6 +117,36 @@ def test_static_batch_matches_planned_batch_on_two_calls():
                 assert np.array_equal(a, b)  # the outcome is unique: compare every byte
             assert np.array_equal(_stored(t_ref), _stored(t_new))
             assert t_new.error_flags() == 0
+            if call == 0:
+                _check_against_oracle(m, t_new, kn.view(np.uint32).astype(np.uint64), b)
+
+
+def test_static_batch_over_many_tables_matches_oracle():
+    # 150 tables: the descriptors go up in three kernel-parameter blocks
+    import paper_2406_09255_gb300 as m
+    rng = np.random.default_rng(5)
+    tables, keys, statuses = [], [], []
+    for i in range(150):
+        e = int(rng.integers(4, 9))
+        tables.append(m.Table(m.ICEBERG, 32, 1 << e, 1 << max(e - 3, 0), key_bytes=4,
+                              fields_per_word=2, seed=3000 + i))
+        size = int(rng.integers(0, 12 * (1 << e)))
+        k = W.duplicate_stream(size, max(size * 7 // 10, 1), 32, 77 + i, 0.3) if size else \
+            torch.zeros(0, dtype=torch.int64)
+        keys.append(W.to_u32(k).to(DEV))
+        statuses.append(torch.empty(max(size, 1), dtype=torch.uint8, device=DEV))
+    for call in range(2):
+        code, L = _static_call(tables, keys, statuses)
+        assert code == m._lib.CHT_OK, L.cht_last_error()
+        torch.cuda.synchronize()
+        for t, k, s in zip(tables, keys, statuses):
+            kn = k.cpu().numpy().view(np.uint32).astype(np.uint64)
+            st = s[: k.numel()].cpu().numpy()
+            if call == 0:
+                _check_against_oracle(m, t, kn, st)
+            else:
+                assert (st == m.FOUND).all()
+            assert t.error_flags() == 0
 
 
 def test_static_batch_rejects_more_tables_than_its_array_holds():
