@@ -70,6 +70,7 @@ class Cfg(ctypes.Structure):
         ("fpw", ctypes.c_int * 2),
         ("nb", ctypes.c_uint64 * 2),
         ("seed", ctypes.c_uint64),
+        ("stash", ctypes.c_uint64),
     ]
 
 
@@ -110,6 +111,8 @@ def lib():
                 "orc_check_order_property": (u64, [_cfgp, _u64p, _u64p]),
                 "orc_check_cuckoo_chain": (u64, [_cfgp, _u64p]),
                 "orc_check_duplicates": (u64, [_cfgp, _u64p, _u64p]),
+                "orc_check_stash": (u64, [_cfgp, _u64p, _u64p]),
+                "orc_stash_home": (u64, [_cfgp, u64]),
                 "orc_set_slot": (None, [_cfgp, i, _u64p, u64, i, u64]),
                 "orc_entry_of": (u64, [_cfgp, i, u64]),
                 "orc_bucket_of": (u64, [_cfgp, i, u64]),
@@ -140,13 +143,14 @@ def _keys(keys) -> np.ndarray:
 
 def make_cfg(kind: int, key_bits: int, nb0: int, nb1: int = 0, *,
              compact: bool = True, fpw0: int = 1, fpw1: int = 1, wpb: int = 16,
-             num_hashes: int = 3, max_chain: int = 128, seed: int = 0) -> Cfg:
+             num_hashes: int = 3, max_chain: int = 128, seed: int = 0, stash: int = 0) -> Cfg:
     c = Cfg()
     c.kind, c.compact, c.key_bits = kind, int(compact), key_bits
     c.num_hashes, c.max_chain, c.wpb = num_hashes, max_chain, wpb
     c.fpw[0], c.fpw[1] = fpw0, (fpw1 if kind == ICEBERG else 1)
     c.nb[0], c.nb[1] = nb0, (nb1 if kind == ICEBERG else 0)
     c.seed = seed & 0xFFFFFFFFFFFFFFFF
+    c.stash = stash if kind == ICEBERG else 0
     return c
 
 
@@ -162,13 +166,16 @@ class Table:
     keys in 64-bit slots. nb0 / nb1: bucket counts of level 0 (the cuckoo
     table or iceberg primary) and level 1 (iceberg secondary). fpw0 / fpw1:
     fields per 64-bit word. wpb: 64-bit words per bucket (16 = 128 bytes).
+    stash: iceberg level-3 overflow slots (0 = none, else a power of two),
+    kept after the secondary level in t1.
     """
 
     def __init__(self, kind: int, key_bits: int, nb0: int, nb1: int = 0, *,
                  compact: bool = True, fpw0: int = 1, fpw1: int = 1, wpb: int = 16,
-                 num_hashes: int = 3, max_chain: int = 128, seed: int = 0):
+                 num_hashes: int = 3, max_chain: int = 128, seed: int = 0, stash: int = 0):
         c = make_cfg(kind, key_bits, nb0, nb1, compact=compact, fpw0=fpw0, fpw1=fpw1,
-                     wpb=wpb, num_hashes=num_hashes, max_chain=max_chain, seed=seed)
+                     wpb=wpb, num_hashes=num_hashes, max_chain=max_chain, seed=seed,
+                     stash=stash)
         self.cfg = c
         self._cp = ctypes.byref(c)
         L = lib()
@@ -322,6 +329,19 @@ class Table:
 
     def check_duplicates(self) -> int:
         return int(lib().orc_check_duplicates(self._cp, _p64(self.t0), _p64(self.t1)))
+
+    def check_stash(self) -> int:
+        return int(lib().orc_check_stash(self._cp, _p64(self.t0), _p64(self.t1)))
+
+    def stash_home(self, k: int) -> int:
+        return int(lib().orc_stash_home(self._cp, k))
+
+    @property
+    def stash(self) -> np.ndarray:
+        """The level-3 stash (whole keys, 0 = empty), a view into t1."""
+        c = self.cfg
+        off = c.nb[1] * c.wpb
+        return self.t1[off: off + c.stash]
 
     def check_prefix_level(self, level: int) -> int:
         t = self.t0 if level == 0 else self.t1

@@ -85,6 +85,8 @@ int orc_cfg_check(const orc_cfg *c)
         return 3;
     if (c->kind == 0 && (c->num_hashes < 1 || c->num_hashes > 3 || c->max_chain < 1))
         return 4;
+    if (c->stash && (c->kind != 1 || (c->stash & (c->stash - 1)) || c->stash > (1ULL << 40)))
+        return 9;
     for (int level = 0; level < levels; level++) {
         int fpw = c->fpw[level];
         uint64_t nb = c->nb[level];
@@ -200,7 +202,22 @@ int orc_prec(int x1, int y1, int x2, int y2)
 
 uint64_t orc_table_words(const orc_cfg *c, int level)
 {
-    return c->nb[level] * (uint64_t)c->wpb;
+    uint64_t w = c->nb[level] * (uint64_t)c->wpb;
+    return level == 1 ? w + c->stash : w;
+}
+
+/* the stash: whole keys after the secondary level's words */
+static uint64_t *orc_stash_ptr(const orc_cfg *c, const uint64_t *t1)
+{
+    return (uint64_t *)t1 + c->nb[1] * (uint64_t)c->wpb;
+}
+
+/* home position of k in the stash: the splitmix64 finaliser of k xor a
+ * constant of the third level (output 16 of the seed's sequence, after the
+ * permutation constants of levels 0 and 1) */
+uint64_t orc_stash_home(const orc_cfg *c, uint64_t k)
+{
+    return orc_mix64(k ^ orc_splitmix(c->seed, 16)) & (c->stash - 1);
 }
 
 int orc_slots_per_bucket(const orc_cfg *c, int level)
@@ -431,6 +448,45 @@ void orc_cuckoo_find_exhaustive(const orc_cfg *c, const uint64_t *table,
 /* Iceberg find-or-put, Algorithm 5 (Appendix A), run sequentially           */
 /* ------------------------------------------------------------------------ */
 
+/* Level 3, reached only when the primary and both secondary buckets are
+ * full (Section 2.3): linear probing in the stash from k's home position;
+ * k found -> FOUND, the first empty position takes k -> PUT, all positions
+ * taken -> FULL. */
+static int orc_stash_fop(const orc_cfg *c, uint64_t *t1, uint64_t k, uint64_t *writes)
+{
+    uint64_t *st = orc_stash_ptr(c, t1);
+    uint64_t h = orc_stash_home(c, k);
+    for (uint64_t i = 0; i < c->stash; i++) {
+        uint64_t p = (h + i) & (c->stash - 1);
+        if (st[p] == k)
+            return ORC_FOUND;
+        if (st[p] == 0) {
+            st[p] = k;
+            (*writes)++;
+            return ORC_PUT;
+        }
+    }
+    return ORC_FULL;
+}
+
+/* lookup in the stash: stops at k or at the first empty position */
+static int orc_stash_find(const orc_cfg *c, const uint64_t *t1, uint64_t k, uint64_t *pos)
+{
+    const uint64_t *st = orc_stash_ptr(c, t1);
+    uint64_t h = orc_stash_home(c, k);
+    for (uint64_t i = 0; i < c->stash; i++) {
+        uint64_t p = (h + i) & (c->stash - 1);
+        if (st[p] == k) {
+            if (pos)
+                *pos = p;
+            return 1;
+        }
+        if (st[p] == 0)
+            return 0;
+    }
+    return 0;
+}
+
 static int orc_iceberg_fop1(const orc_cfg *c, uint64_t *t0, uint64_t *t1,
                             uint64_t k, uint64_t *probes, uint64_t *writes)
 {
@@ -468,7 +524,7 @@ static int orc_iceberg_fop1(const orc_cfg *c, uint64_t *t0, uint64_t *t1,
             }
         }
     if (bx < 0)
-        return ORC_FULL;
+        return c->stash ? orc_stash_fop(c, t1, k, writes) : ORC_FULL;
     orc_set_slot(c, bx ? 1 : 0, bx ? t1 : t0, a[bx], by, e[bx]);
     (*writes)++;
     return ORC_PUT;
@@ -517,11 +573,17 @@ void orc_iceberg_find(const orc_cfg *c, const uint64_t *t0, const uint64_t *t1,
             continue;
         }
         p += 2;
-        int hit = 0;
-        for (int x = 1; x <= 2; x++)
-            if (orc_bucket_contains(c, 1, t1, orc_iceberg_bucket(c, x, k),
-                                    orc_iceberg_entry(c, x, k)))
+        int hit = 0, room = 0;
+        for (int x = 1; x <= 2; x++) {
+            uint64_t a = orc_iceberg_bucket(c, x, k);
+            if (orc_bucket_contains(c, 1, t1, a, orc_iceberg_entry(c, x, k)))
                 hit = 1;
+            room |= orc_bucket_has_empty(c, 1, t1, a);
+        }
+        /* level 3: k can be in the stash only if all three buckets were full
+         * when it was put, and full buckets stay full */
+        if (!hit && !room && c->stash)
+            hit = orc_stash_find(c, t1, k, NULL);
         status[i] = hit ? ORC_FOUND : ORC_NOT_FOUND;
     }
     if (probes)
@@ -534,8 +596,8 @@ void orc_iceberg_find(const orc_cfg *c, const uint64_t *t0, const uint64_t *t1,
 /* ------------------------------------------------------------------------ */
 
 /* Level-0 slots are numbered a * B0 + y, level-1 slots nb0 * B0 + a * B1 + y,
- * with y the slot's position in bucket a. Absent or invalid keys get
- * UINT64_MAX. */
+ * with y the slot's position in bucket a, and stash position p is
+ * nb0 * B0 + nb1 * B1 + p. Absent or invalid keys get UINT64_MAX. */
 void orc_iceberg_locate(const orc_cfg *c, const uint64_t *t0, const uint64_t *t1,
                         const uint64_t *keys, size_t n, uint64_t *slot_out)
 {
@@ -561,6 +623,9 @@ void orc_iceberg_locate(const orc_cfg *c, const uint64_t *t0, const uint64_t *t1
                 }
             }
         }
+        uint64_t p;
+        if (slot_out[i] == UINT64_MAX && c->stash && orc_stash_find(c, t1, k, &p))
+            slot_out[i] = c->nb[0] * (uint64_t)B0 + c->nb[1] * (uint64_t)B1 + p;
     }
 }
 
@@ -612,6 +677,16 @@ uint64_t orc_enumerate(const orc_cfg *c, const uint64_t *t0,
                     out[cnt] = k;
                 cnt++;
             }
+    }
+    if (c->kind == 1 && c->stash) {
+        const uint64_t *st = orc_stash_ptr(c, t1);
+        for (uint64_t p = 0; p < c->stash; p++) {
+            if (st[p] == 0)
+                continue;
+            if (cnt < cap)
+                out[cnt] = st[p];
+            cnt++;
+        }
     }
     return cnt;
 }
@@ -726,6 +801,38 @@ uint64_t orc_check_cuckoo_chain(const orc_cfg *c, const uint64_t *table)
                     break;
                 }
         }
+    return bad;
+}
+
+uint64_t orc_check_stash(const orc_cfg *c, const uint64_t *t0,
+                         const uint64_t *t1)
+{
+    uint64_t bad = 0;
+    if (c->kind != 1 || !c->stash)
+        return 0;
+    const uint64_t *st = orc_stash_ptr(c, t1);
+    for (uint64_t p = 0; p < c->stash; p++) {
+        uint64_t k = st[p];
+        if (k == 0)
+            continue;
+        int violated = !orc_valid_key(c, k);
+        /* stash slots come after every bucket slot: all three buckets full,
+         * none holding k */
+        for (int x = 0; x < 3 && !violated; x++) {
+            int level = x ? 1 : 0;
+            const uint64_t *t = orc_level_table(x, t0, t1);
+            uint64_t a = orc_iceberg_bucket(c, x, k);
+            if (orc_bucket_has_empty(c, level, t, a) ||
+                orc_bucket_contains(c, level, t, a, orc_iceberg_entry(c, x, k)))
+                violated = 1;
+        }
+        /* linear probing: every position from home up to p holds another key */
+        for (uint64_t q = orc_stash_home(c, k); q != p && !violated;
+             q = (q + 1) & (c->stash - 1))
+            if (st[q] == 0 || st[q] == k)
+                violated = 1;
+        bad += (uint64_t)violated;
+    }
     return bad;
 }
 
@@ -865,6 +972,30 @@ static uint64_t *mt_word(const orc_cfg *c, int level, uint64_t *table,
     return &table[a * (uint64_t)c->wpb + (uint64_t)(y / c->fpw[level])];
 }
 
+/* level 3 with compare-and-swap claims: linear probing from k's home; a
+ * position that another thread filled first is read again (k itself means
+ * FOUND) and otherwise passed */
+static int mt_stash_fop(const orc_cfg *c, uint64_t *t1, uint64_t k, uint64_t *fails)
+{
+    uint64_t *st = orc_stash_ptr(c, t1);
+    uint64_t h = orc_stash_home(c, k);
+    for (uint64_t i = 0; i < c->stash; i++) {
+        uint64_t *sp = &st[(h + i) & (c->stash - 1)];
+        uint64_t v = mt_load(sp);
+        if (v == 0) {
+            uint64_t expected = 0;
+            if (__atomic_compare_exchange_n(sp, &expected, k, 0, __ATOMIC_RELAXED,
+                                            __ATOMIC_RELAXED))
+                return ORC_PUT;
+            (*fails)++;
+            v = expected;
+        }
+        if (v == k)
+            return ORC_FOUND;
+    }
+    return ORC_FULL;
+}
+
 /* Algorithm 1 for one key, with the claims above */
 static int mt_iceberg_fop1(const orc_cfg *c, uint64_t *t0, uint64_t *t1,
                            uint64_t k, uint64_t *fails)
@@ -906,7 +1037,7 @@ static int mt_iceberg_fop1(const orc_cfg *c, uint64_t *t0, uint64_t *t1,
         int pick1 = y1 < y2;
         int y = pick1 ? y1 : y2;
         if (y == B1)
-            return ORC_FULL;
+            return c->stash ? mt_stash_fop(c, t1, k, fails) : ORC_FULL;
         uint64_t a = pick1 ? a1 : a2, e = pick1 ? e1 : e2;
         uint64_t *snap = pick1 ? w1 : w2;
         uint64_t seen = 0;

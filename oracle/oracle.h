@@ -15,6 +15,14 @@
  * primary level; level 1 is the iceberg secondary (backyard) level. Slot y of
  * a bucket lives in word y / fpw, bits [(y % fpw) * s, (y % fpw) * s + s),
  * where fpw is the number of fields per word and s = 64 / fpw.
+ *
+ * An iceberg table may have a third level (Section 2.3 describes it; the
+ * paper's implementation leaves it out, Section 3): an overflow stash of
+ * `stash` whole-key slots stored after the secondary level's words in the
+ * level-1 array. A key goes there only when its primary and both secondary
+ * buckets are full; the stash is an open-addressing table with linear
+ * probing from a hash of the key (this library's design: the paper gives
+ * none).
  */
 #ifndef CHT_ORACLE_H
 #define CHT_ORACLE_H
@@ -45,6 +53,8 @@ typedef struct {
     int fpw[2];        /* fields per 64-bit word, per level                    */
     uint64_t nb[2];    /* bucket counts, per level (nb[1] = 0 for cuckoo)      */
     uint64_t seed;     /* all permutation constants derive from this           */
+    uint64_t stash;    /* iceberg level-3 overflow stash: 0 (none) or a power  */
+                       /* of two, its slot count                               */
 } orc_cfg;
 
 /* 0 if the configuration is usable: every encoded entry fits its field, the
@@ -68,7 +78,10 @@ void orc_perm_many(const orc_cfg *c, int level, int j, const uint64_t *keys,
 int orc_prec(int x1, int y1, int x2, int y2);
 
 /* --- table geometry --- */
+/* words of a level's array (level 1 includes the stash, if any) */
 uint64_t orc_table_words(const orc_cfg *c, int level);
+/* first stash position of key k (linear probing continues from it) */
+uint64_t orc_stash_home(const orc_cfg *c, uint64_t k);
 int orc_slots_per_bucket(const orc_cfg *c, int level);
 uint64_t orc_get_slot(const orc_cfg *c, int level, const uint64_t *table,
                       uint64_t bucket, int y);
@@ -126,6 +139,9 @@ uint64_t orc_check_order_property(const orc_cfg *c, const uint64_t *t0,
                                   const uint64_t *t1);
 /* cuckoo: an entry stored under hash index j has buckets a_0..a_{j-1} full */
 uint64_t orc_check_cuckoo_chain(const orc_cfg *c, const uint64_t *table);
+/* level-3 stash: every stash key has its three buckets full without it, and
+ * every position from its home up to its own holds another key */
+uint64_t orc_check_stash(const orc_cfg *c, const uint64_t *t0, const uint64_t *t1);
 /* stored entries minus distinct stored keys (0 when no key is held twice) */
 uint64_t orc_check_duplicates(const orc_cfg *c, const uint64_t *t0,
                               const uint64_t *t1);

@@ -78,6 +78,24 @@ MUTATIONS = [
      "int pick1 = y1 < y2;", "int pick1 = y1 <= y2;"),
     ("threaded claim takes a lost field as its own",
      "        if (fld != 0) {\n            *seen = fld;", "        if (fld != 0) {\n            *seen = e;"),
+    # mistakes in the level-3 stash
+    ("stash put only tries the home position",
+     "    for (uint64_t i = 0; i < c->stash; i++) {\n        uint64_t p = (h + i) & (c->stash - 1);\n"
+     "        if (st[p] == k)\n            return ORC_FOUND;",
+     "    for (uint64_t i = 0; i < 1; i++) {\n        uint64_t p = (h + i) & (c->stash - 1);\n"
+     "        if (st[p] == k)\n            return ORC_FOUND;"),
+    ("lookup never reaches the stash",
+     "if (!hit && !room && c->stash)", "if (!hit && !room && 0)"),
+    ("enumeration forgets the stash",
+     "if (c->kind == 1 && c->stash) {", "if (c->kind == 1 && 0) {"),
+    ("stash home from the wrong constant",
+     "orc_mix64(k ^ orc_splitmix(c->seed, 16))", "orc_mix64(k ^ orc_splitmix(c->seed, 15))"),
+    ("threaded stash claim without a compare-and-swap",
+     "            if (__atomic_compare_exchange_n(sp, &expected, k, 0, __ATOMIC_RELAXED,\n"
+     "                                            __ATOMIC_RELAXED))\n                return ORC_PUT;",
+     "            __atomic_store_n(sp, k, __ATOMIC_RELAXED);\n                return ORC_PUT;"),
+    ("stash checker ignores gaps on the probe path",
+     "if (st[q] == 0 || st[q] == k)", "if (st[q] == k)"),
     ("duplicates checker skips the first pair",
      "for (uint64_t i = 1; i < n; i++)\n        if (keys[i] == keys[i - 1])",
      "for (uint64_t i = 2; i < n; i++)\n        if (keys[i] == keys[i - 1])"),
@@ -103,7 +121,8 @@ def _scratch(tmp_path, old=None, new=None):
 
 
 def _run_pins(dst) -> int:
-    env = dict(os.environ, PYTHONPATH=str(dst))
+    # the scratch oracle first; the package (input generators) from the repo
+    env = dict(os.environ, PYTHONPATH=f"{dst}{os.pathsep}{ROOT}")
     r = subprocess.run([sys.executable, "-m", "pytest", "tests", "-q", "-x",
                         "-p", "no:cacheprovider"], cwd=dst, env=env,
                        stdout=subprocess.PIPE, stderr=subprocess.STDOUT, timeout=600)
