@@ -298,6 +298,30 @@ def random_read_ceiling(dev, block_bytes=128, n_blocks=1 << 28, buf_bytes=1 << 3
     return n_blocks / (statistics.median(times) * 1e-3)
 
 
+def random_claim_ceiling(dev, n_lines=1 << 28, buf_bytes=1 << 31):
+    """Rate (lines per second) at which device memory serves the access
+    pattern of a put that claims a slot in the first bucket it probes: a
+    random 128-byte line read, then a compare-and-swap into that line
+    (cht_random_claim): the ceiling for puts."""
+    from paper_2406_09255_gb300 import _lib
+    L = _lib.load()
+    buf = torch.zeros(buf_bytes, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    s = torch.cuda.current_stream(dev)
+    times = []
+    for rep in range(4):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        _lib.check(L.cht_random_claim(buf.data_ptr(), buf.numel(), n_lines, rep,
+                                      sink.data_ptr(), ctypes.c_void_p(s.cuda_stream)))
+        b.record(s)
+        torch.cuda.synchronize(dev)
+        if rep:
+            times.append(a.elapsed_time(b))
+    del buf
+    return n_lines / (statistics.median(times) * 1e-3)
+
+
 def run_random_read(args, dev):
     """Random-access rate of HBM by block size (cht_random_read over a 2 GiB
     buffer, and over a 32 MiB L2-resident one): the ceiling behind every
@@ -309,8 +333,10 @@ def run_random_read(args, dev):
         out["results"][f"hbm_{bb}B"] = {"g_blocks_per_s": r / 1e9, "gbs": r * bb / 1e9}
     r = random_read_ceiling(dev, block_bytes=128, buf_bytes=1 << 25)
     out["results"]["l2_128B"] = {"g_blocks_per_s": r / 1e9, "gbs": r * 128 / 1e9}
+    r = random_claim_ceiling(dev)
+    out["results"]["hbm_128B_read_then_cas"] = {"g_lines_per_s": r / 1e9}
     out["value"] = out["results"]["hbm_128B"]["g_blocks_per_s"]
-    print(json.dumps(out))
+    return out
 
 
 def run_e2e(wl, steps, warmup, direct=False):
@@ -587,7 +613,7 @@ def run_iceberg_stream(args, dev):
                         "bytes_model": "128 B per probe + 32 B per slot write + 9 B per op"},
            "probes_per_op": probes / ops, "writes_per_op": writes / ops,
            "final_fill": int(t.enumerate()[1]) / slots, "clocks": clk}
-    print(json.dumps(out))
+    return out
 
 
 def run_batch256(args, dev):
@@ -650,7 +676,7 @@ def run_batch256(args, dev):
            "speedup_fused_vs_per_table": ms_per / ms_fused, "tuned": {k: tuned[k] for k in
                                                                       ("tile", "items", "cached")},
            "contract_ok": ok}
-    print(json.dumps(out))
+    return out
 
 
 def run_iceberg_variants(args, dev):
@@ -723,7 +749,7 @@ def run_iceberg_variants(args, dev):
                                   "buckets; 16/32-bit, 32/32-bit and 64/64-bit slots; fills "
                                   "0.5/0.7/0.8/0.9; 2^26 lookups at 50% hit per fill"},
            "results": results}
-    print(json.dumps(out))
+    return out
 
 
 def run_kv(args, dev):
@@ -786,7 +812,7 @@ def run_kv(args, dev):
                                   "8-byte values, put to fill 0.8 in 2^24-key batches, 2^26 "
                                   "gets at 50% hit"},
            "results": res}
-    print(json.dumps(out))
+    return out
 
 
 def run_served(args, dev):
@@ -854,7 +880,7 @@ def run_served(args, dev):
                                   f"{n_req} requests, log-uniform 256..4M keys, 60/30/10 find/"
                                   f"fop/insert, 40% re-queries, Poisson arrivals"},
            "saturated_request_rate": sat_rate, "results": results}
-    print(json.dumps(out))
+    return out
 
 
 def run_profile_case(kind: str, dev):
@@ -897,6 +923,88 @@ def run_profile_case(kind: str, dev):
                       "max_gib": torch.cuda.max_memory_allocated(dev) / 2 ** 30}))
 
 
+def run_whole_key(args, dev, name):
+    """The headline step on one of the whole-key cuckoo tables (equal memory
+    or equal slot count), timed per phase with CUDA events."""
+    spec = WORKLOADS[name]
+    wl = Workload(name, spec, dev)
+    wl.step()
+    torch.cuda.synchronize()
+    evs = []
+    a, b = _events()
+    a.record()
+    for _ in range(args.steps):
+        wl.step(evs)
+    b.record()
+    torch.cuda.synchronize()
+    ph = {}
+    for key, e0, e1 in evs:
+        ph.setdefault(key, []).append(e0.elapsed_time(e1))
+    rows = []
+    for fi, f in enumerate(spec["fills"]):
+        n_ins = wl.n_f[fi] - (wl.n_f[fi - 1] if fi else 0)
+        row = {"fill": f, "insert_mops": n_ins / statistics.median(ph[("insert", fi, n_ins)]) / 1e3}
+        for hi, h in enumerate(spec["hits"]):
+            row[f"find{int(h * 100)}_mops"] = wl.nq / statistics.median(ph[("find", fi, hi)]) / 1e3
+        rows.append(row)
+    failed = int((wl.st_ins != 2).sum().item())
+    res = {"table_bytes": int(wl.t.storage.numel()), "slots": wl.slots,
+           "num_buckets": spec["num_buckets"], "ms_per_step": a.elapsed_time(b) / args.steps,
+           "mops": wl.ops_per_step * args.steps / a.elapsed_time(b) / 1e3,
+           "failed_inserts_last_step": failed, "phases": rows}
+    del wl
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
+
+
+def extra_configs(args, dev, compact_phases):
+    """The other configurations, after the headline and outside its timed
+    region, each with its own clock samples: the same library's whole-key
+    cuckoo tables (equal memory, equal slots), the iceberg find-or-put
+    stream, the 256-table fused batch and the served request loop."""
+    import argparse as _ap
+    res = {}
+
+    def section(name, fn):
+        clocks = Clocks(dev.index or 0)
+        clocks.start()
+        t0 = time.perf_counter()
+        try:
+            r = fn()
+        except Exception as e:  # recorded in the line, never hidden
+            r = {"error": f"{type(e).__name__}: {e}"}
+        r["clocks"] = clocks.stop()
+        r["wall_s"] = time.perf_counter() - t0
+        res[name] = r
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+    few = _ap.Namespace(steps=3, warmup=1, requests=args.requests)
+    section("cuckoo_whole_key_equal_memory",
+            lambda: run_whole_key(few, dev, "cuckoo_2e24_noncompact_mem"))
+    section("cuckoo_whole_key_equal_slots",
+            lambda: run_whole_key(few, dev, "cuckoo_2e24_noncompact_slots"))
+    # compact vs whole key per fill (G ops/s ratios, > 1: compact faster)
+    cmp_rows = []
+    for i, c in enumerate(compact_phases):
+        row = {"fill": c["fill"]}
+        for key in ("cuckoo_whole_key_equal_memory", "cuckoo_whole_key_equal_slots"):
+            ph = res[key].get("phases")
+            if not ph:
+                continue
+            tag = "mem" if key.endswith("memory") else "slots"
+            row[f"insert_vs_{tag}"] = c["insert_mops"] / ph[i]["insert_mops"]
+            for h in ("find0", "find50", "find100"):
+                row[f"{h}_vs_{tag}"] = c[f"{h}_mops"] / ph[i][f"{h}_mops"]
+        cmp_rows.append(row)
+    res["compact_over_whole_key"] = cmp_rows
+    section("iceberg_stream", lambda: run_iceberg_stream(_ap.Namespace(steps=3, warmup=1), dev))
+    section("batch256", lambda: run_batch256(_ap.Namespace(steps=5, warmup=2), dev))
+    section("served", lambda: run_served(few, dev))
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -909,6 +1017,9 @@ def main():
     ap.add_argument("--workload", default="cuckoo_2e24", choices=sorted(WORKLOADS) + sorted(others))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other configurations (whole-key tables, iceberg stream, "
+                         "256-table batch, served loop) that follow the headline")
     ap.add_argument("--requests", type=int, default=4000, help="served workload: request count")
     ap.add_argument("--profile", choices=["find", "insert", "fop"],
                     help="run a small case for an ncu capture and exit")
@@ -926,7 +1037,7 @@ def main():
         torch.cuda.set_device(dev)
         import __graft_entry__
         __graft_entry__.build()
-        others[args.workload](args, dev)
+        print(json.dumps(others[args.workload](args, dev)))
         return 0
     spec = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -984,9 +1095,13 @@ def main():
         n_ins = wl.n_f[fi] - (wl.n_f[fi - 1] if fi else 0)
         ims = statistics.median(ph[("insert", fi, n_ins)])
         p, wr, cf, ops = counts[("insert", fi)]
+        ins_bytes = 128.0 * p + 32.0 * wr + 9.0 * n_ins
         entry = {"fill": f, "insert_mops": n_ins / ims / 1e3,
                  "insert_probes_per_op": p / max(ops, 1),
                  "insert_writes_per_op": wr / max(ops, 1),
+                 # per-probe HBM roofline of the puts: a line per probe, a
+                 # 32-byte sector written back per slot write, key and status
+                 "insert_hbm_frac": ins_bytes / (ims * 1e-3) / 1e9 / peak,
                  # a put reads its line and later writes back the dirtied sector:
                  # two random DRAM accesses per probe-and-write
                  "insert_random_accesses_per_s": (p + wr) / (ims * 1e-3),
@@ -1007,8 +1122,12 @@ def main():
     achieved = fb / (fms * 1e-3) / 1e9
     ceiling = random_read_ceiling(dev)
     probe_rate = fprobes / (fms * 1e-3)
+    put_ceiling = random_claim_ceiling(dev)
     for entry in phases:
         entry["insert_frac_of_random_ceiling"] = entry["insert_random_accesses_per_s"] / ceiling
+        # puts per second over the measured rate of (random line read + a
+        # compare-and-swap into it): the put ceiling
+        entry["insert_frac_of_put_ceiling"] = entry["insert_mops"] * 1e6 / put_ceiling
     launches = len([1 for k in ph if k[0] == "find"])
     tpu = traffic_per_unit("cuckoo_find")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -1019,7 +1138,11 @@ def main():
                                   "ceiling_lines_per_s": ceiling,
                                   "frac_of_ceiling": probe_rate / ceiling if ceiling else None,
                                   "ceiling_source": "cht_random_read: 2^28 random 128-byte "
-                                                    "line reads over a 2 GiB buffer, median of 3"}}
+                                                    "line reads over a 2 GiB buffer, median of 3"},
+                "put_ceiling": {"lines_per_s": put_ceiling,
+                                "source": "cht_random_claim: 2^28 random 128-byte line reads, "
+                                          "each followed by a compare-and-swap into the line, "
+                                          "over a 2 GiB buffer, median of 3"}}
 
     e2e = None
     if not args.no_e2e:
@@ -1027,10 +1150,20 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec)
+    headline_ops = wl.ops_per_step
+    headline_launches = wl.launches_per_step
+    describe_line = describe(args.workload, spec, wl.slots)
+    tile, items = wl.t.cfg.tile, wl.t.cfg.items_per_thread
+    del wl
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    extra = None
+    if not args.no_extra and ws == 1 and args.workload == "cuckoo_2e24":
+        extra = extra_configs(args, dev, phases)
 
     out = {
         "metric": METRIC,
-        "value": job_rate_mops(wl.ops_per_step, args.steps, ws, ms_max),
+        "value": job_rate_mops(headline_ops, args.steps, ws, ms_max),
         "unit": "Mops/s",
         "n_gpus": ws,
         "steps": args.steps,
@@ -1043,17 +1176,19 @@ def main():
         "vs_baseline": None,
         "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": describe(args.workload, spec, wl.slots),
+        "config": {"workload": describe_line,
                    "l2": "inputs larger than L2 (2 GiB table, >= 3.2 GB key arrays)",
-                   "tile": wl.t.cfg.tile, "items_per_thread": wl.t.cfg.items_per_thread,
+                   "tile": tile, "items_per_thread": items,
                    "parallelism": f"replicas x{ws}"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": wl.launches_per_step * args.steps,
+        "gpu_launches": headline_launches * args.steps,
         "clocks": clk,
         "phases": phases,
     }
+    if extra is not None:
+        out["other_configs"] = extra
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:

@@ -120,6 +120,18 @@ typedef struct cht_table cht_table; /* opaque host handle */
  *                       test drive the error path (CHT_ERROR statuses and
  *                       cht_error_flags) under contention; set it at
  *                       cht_create. Cuckoo tables ignore it.
+ * stash_slots           iceberg level-3 overflow stash (Section 2.3 describes
+ *                       a third level; the paper's implementation leaves it
+ *                       out): 0 = none, else a power of two in [2, 2^30],
+ *                       the number of whole-key slots. A key goes there only
+ *                       when its primary and both secondary buckets are full
+ *                       (a two-level table would report CHT_FULL); the stash
+ *                       is an open-addressing table with linear probing from
+ *                       a hash of the key, claimed by 64-bit compare-and-swap,
+ *                       so find-or-put still reports exactly one CHT_PUT per
+ *                       absent key and CHT_FULL only once the key's probe
+ *                       sequence holds no free slot. Cuckoo tables must
+ *                       leave it 0.
  */
 typedef struct cht_config {
     int32_t kind;
@@ -140,7 +152,7 @@ typedef struct cht_config {
     int32_t max_tiles;
     int32_t lookups_in_flight;
     int32_t retry_limit;
-    int32_t reserved;
+    int32_t stash_slots;
 } cht_config;
 
 /* Device counters a table can accumulate into (see cht_set_counters). */
@@ -160,8 +172,9 @@ int cht_resolve_config(const cht_config *cfg, cht_config *out);
 /*
  * Bytes of device storage a table of this configuration needs:
  * CHT_HEADER_BYTES + (num_buckets + num_buckets_backyard) * CHT_BUCKET_BYTES
- * (no backyard for cuckoo). Returns 0 if the configuration is invalid.
- * Host only.
+ * (no backyard for cuckoo), plus 8 * stash_slots rounded up to a multiple of
+ * CHT_BUCKET_BYTES for an iceberg stash. Returns 0 if the configuration is
+ * invalid. Host only.
  */
 size_t cht_table_bytes(const cht_config *cfg);
 
@@ -240,8 +253,9 @@ int cht_find_or_put(cht_table *t, const void *d_keys, size_t n,
  * slot y of secondary bucket a is nb0 * B0 + a * B1 + y, where B0 = 16 *
  * fields_per_word and B1 = 16 * fields_per_word_backyard are the slots per
  * bucket and y runs over a bucket's slots in slot order (word by word, field
- * by field). There are nb0 * B0 + nb1 * B1 slots in all. A key keeps its slot
- * for the table's lifetime (until cht_clear). d_slots: n device uint64
+ * by field); stash position p (level 3, when the table has a stash) is slot
+ * nb0 * B0 + nb1 * B1 + p. There are nb0 * B0 + nb1 * B1 + stash_slots slots
+ * in all. A key keeps its slot for the table's lifetime (until cht_clear). d_slots: n device uint64
  * (8-byte aligned), written. Iceberg tables only (CHT_ERR_UNSUPPORTED on
  * cuckoo tables, whose puts move entries); other arguments and errors as for
  * cht_find_or_put / cht_find.
@@ -274,7 +288,7 @@ int cht_values_gather(const uint64_t *d_slots, size_t n, const void *d_store, in
  * FULL keys store nothing). cht_kv_get = cht_find, then d_out[i] =
  * d_store[slot(i)] for FOUND keys and zero otherwise. d_store holds
  * store_slots values of value_bytes (4, 8 or 16) and must cover the table's
- * slots (nb0 * B0 + nb1 * B1, see above) for every key to have its value;
+ * slots (nb0 * B0 + nb1 * B1 + stash_slots, see above) for every key to have its value;
  * slots at or past store_slots are skipped. Iceberg tables only
  * (CHT_ERR_UNSUPPORTED otherwise); values aligned to value_bytes
  * (CHT_ERR_INVALID otherwise); keys, statuses and errors as for
@@ -389,7 +403,7 @@ int cht_batch_destroy(cht_batch *b);
  *
  * The batch descriptors live in a fixed array inside the library (device
  * memory that every GPU which loads the library holds until the process
- * exits) with room for CHT_STATIC_BATCH_MAX tables (224 bytes each, 56 KiB in
+ * exits) with room for CHT_STATIC_BATCH_MAX tables (240 bytes each, 60 KiB in
  * all); count above that is rejected with CHT_ERR_INVALID. Nothing is
  * allocated on any call: the descriptors travel to the array as the
  * parameters of small kernel launches on stream (so the host never waits),
@@ -430,6 +444,24 @@ const char *cht_version(void);
  */
 int cht_random_read(const void *d_buf, size_t buf_bytes, int block_bytes, uint64_t n_blocks,
                     uint64_t seed, uint64_t *d_sink, void *stream);
+
+/*
+ * Measurement utility; the paper has no counterpart. The access pattern of a
+ * put that claims a slot in the first bucket it probes: for each of n_lines
+ * pseudo-random 128-byte lines of d_buf (splitmix64 of seed + i, masked to
+ * the line count), eight lanes read the line with 16-byte relaxed loads, then
+ * the lane owning one of its words (chosen from the same hash) compare-and-
+ * swaps that word from the value it read to that value + 1; four lines per
+ * tile in flight, the four compare-and-swaps issued before any result is
+ * read, as the put kernels do. Timed with events on stream, it gives the
+ * rate at which this GPU's memory serves a line read plus the write-back of
+ * the dirtied line: the ceiling for puts. d_buf: device memory of buf_bytes =
+ * 128 x a power of two, 128-byte aligned, modified; d_sink: one 8-byte aligned
+ * device word, modified. Asynchronous on stream; CHT_ERR_INVALID on bad
+ * arguments, CHT_ERR_CUDA if the launch fails.
+ */
+int cht_random_claim(void *d_buf, size_t buf_bytes, uint64_t n_lines, uint64_t seed,
+                     uint64_t *d_sink, void *stream);
 
 #ifdef __cplusplus
 }

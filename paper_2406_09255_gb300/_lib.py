@@ -40,11 +40,11 @@ class Config(ctypes.Structure):
         ("max_tiles", ctypes.c_int32),
         ("lookups_in_flight", ctypes.c_int32),
         ("retry_limit", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("stash_slots", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Counters(ctypes.Structure):
@@ -87,6 +87,7 @@ SIGNATURES = {
     "cht_version": (ctypes.c_char_p, []),
     "cht_random_read": (ctypes.c_int, [_vp, _sz, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                        _vp, _vp]),
+    "cht_random_claim": (ctypes.c_int, [_vp, _sz, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp]),
     "cht_find_or_put_slots": (ctypes.c_int, [_vp, _vp, _sz, _vp, _vp, _vp]),
     "cht_find_slots": (ctypes.c_int, [_vp, _vp, _sz, _vp, _vp, _vp]),
     "cht_values_scatter": (ctypes.c_int, [_vp, _sz, _vp, ctypes.c_int, _vp, ctypes.c_uint64, _vp]),

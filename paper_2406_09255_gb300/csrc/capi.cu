@@ -137,6 +137,13 @@ int resolve(const cht_config *in, cht_config *out) {
         return fail(CHT_ERR_INVALID, "max_ctas and max_tiles must be >= 0");
     if (c.retry_limit < 0 || c.retry_limit > 32767)
         return fail(CHT_ERR_INVALID, "retry_limit must be 0..32767");
+    if (c.stash_slots != 0) {
+        if (c.kind != CHT_ICEBERG)
+            return fail(CHT_ERR_INVALID, "stash_slots: only iceberg tables have a stash");
+        if (c.stash_slots < 2 || c.stash_slots > (1 << 30) ||
+            !is_pow2((uint64_t)c.stash_slots))
+            return fail(CHT_ERR_INVALID, "stash_slots must be 0 or a power of two in [2, 2^30]");
+    }
     if (c.lookups_in_flight == 0) c.lookups_in_flight = 4;
     if (c.lookups_in_flight != 1 && c.lookups_in_flight != 4 && c.lookups_in_flight != 8)
         return fail(CHT_ERR_INVALID, "lookups_in_flight must be 1, 4 or 8");
@@ -144,9 +151,14 @@ int resolve(const cht_config *in, cht_config *out) {
     return CHT_OK;
 }
 
+// bytes of the stash region: 8 per slot, rounded up to whole 128-byte lines
+uint64_t stash_bytes(const cht_config &c) {
+    return ((uint64_t)c.stash_slots + 15) / 16 * CHT_BUCKET_BYTES;
+}
+
 size_t table_bytes(const cht_config &c) {
     uint64_t nb = c.num_buckets + (c.kind == CHT_ICEBERG ? c.num_buckets_backyard : 0);
-    return CHT_HEADER_BYTES + (size_t)nb * CHT_BUCKET_BYTES;
+    return CHT_HEADER_BYTES + (size_t)nb * CHT_BUCKET_BYTES + (size_t)stash_bytes(c);
 }
 
 void fill_level(Level &L, uint64_t *words, uint64_t nb, int key_bits, int fpw, uint64_t seed,
@@ -267,6 +279,10 @@ int cht_create(const cht_config *cfg, void *d_mem, size_t bytes, void *stream, c
     a.max_tiles = c.max_tiles;
     a.err = reinterpret_cast<uint32_t *>(t->mem);
     a.ctr = nullptr;
+    a.stash_slots = (uint64_t)c.stash_slots;
+    // output 16 of the seed's splitmix64 sequence, after the permutation
+    // constants of levels 0 and 1 (outputs 0..13)
+    a.stash_key = splitmix(c.seed, 16);
     e = clear_storage(t, static_cast<cudaStream_t>(stream));
     if (e) {
         delete t;
@@ -461,7 +477,8 @@ int cht_enumerate(const cht_table *t, void *d_out, size_t cap, uint64_t *d_count
     k_zero_u64<<<1, 32, 0, s>>>(cnt);
     const uint64_t words = (t->cfg.num_buckets +
                             (t->cfg.kind == CHT_ICEBERG ? t->cfg.num_buckets_backyard : 0)) *
-                           kWordsPerBucket;
+                               kWordsPerBucket +
+                           stash_bytes(t->cfg) / 8;
     uint64_t blocks = (words / 2 + 255) / 256;
     const uint64_t cap_blocks = (uint64_t)t->sms * 8;
     if (blocks > cap_blocks) blocks = cap_blocks;
@@ -508,6 +525,24 @@ int cht_random_read(const void *d_buf, size_t buf_bytes, int block_bytes, uint64
                                reinterpret_cast<unsigned long long *>(d_sink), sms,
                                static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? ok() : cuda_fail(e, "random read kernel launch");
+}
+
+int cht_random_claim(void *d_buf, size_t buf_bytes, uint64_t n_lines, uint64_t seed,
+                     uint64_t *d_sink, void *stream) {
+    if (!d_buf || !d_sink) return fail(CHT_ERR_INVALID, "null buffer");
+    if ((reinterpret_cast<uintptr_t>(d_buf) % 128) || (reinterpret_cast<uintptr_t>(d_sink) % 8))
+        return fail(CHT_ERR_INVALID, "d_buf must be 128-byte and d_sink 8-byte aligned");
+    if (buf_bytes % 128 || !is_pow2(buf_bytes / 128))
+        return fail(CHT_ERR_INVALID, "buf_bytes must be 128 times a power of two");
+    if (n_lines == 0) return ok();
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = launch_random_claim(d_buf, buf_bytes, n_lines, seed,
+                                reinterpret_cast<unsigned long long *>(d_sink), sms,
+                                static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "random claim kernel launch");
 }
 
 }  // extern "C"
@@ -731,8 +766,8 @@ int cht_batch_destroy(cht_batch *b) {
 // ---------------------------------------------------------------------------
 namespace {
 
-// the descriptor layout the documented limit is stated in (256 x 224 bytes)
-static_assert(sizeof(BatchDesc) == 224, "batch descriptor size changed: update cht.h");
+// the descriptor layout the documented limit is stated in (256 x 240 bytes)
+static_assert(sizeof(BatchDesc) == 240, "batch descriptor size changed: update cht.h");
 
 // room for CHT_STATIC_BATCH_MAX descriptors; held by every GPU that loads the
 // library until the process exits
@@ -840,7 +875,7 @@ extern "C" int cht_batch_find_or_put_static(cht_table *const *tables, const void
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     BatchDesc *dev_desc = static_cast<BatchDesc *>(dst);
     // descriptors travel as kernel parameters, kDescPerLaunch per launch (a
-    // block of 64 x 224 bytes = 14 KiB on the stack), as in cht_batch_create:
+    // block of 64 x 240 bytes = 15 KiB on the stack), as in cht_batch_create:
     // the upload is an ordinary asynchronous launch on stream
     for (int i0 = 0; i0 < count; i0 += kDescPerLaunch) {
         const int m = std::min(kDescPerLaunch, count - i0);

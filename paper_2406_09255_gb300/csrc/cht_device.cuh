@@ -43,7 +43,7 @@ struct Level {
     uint64_t B[3];    // Feistel round-function offsets, per hash
 };
 
-// Everything a kernel needs about a table, passed by value (200 bytes; a
+// Everything a kernel needs about a table, passed by value (216 bytes; a
 // batch descriptor of the fused launch embeds it).
 struct TableArgs {
     Level lv[2];
@@ -56,6 +56,8 @@ struct TableArgs {
     int max_tiles;            // 0 = unbounded
     uint32_t *err;            // header error word
     unsigned long long *ctr;  // optional cht_counters (probes, writes, cas_fail, ops)
+    uint64_t stash_slots;     // iceberg level-3 stash: 0 = none, else a power of two
+    uint64_t stash_key;       // constant of the stash's home hash
 };
 
 // Lost claims an iceberg find-or-put may retry before it reports ST_ERROR.
@@ -77,6 +79,69 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 __host__ __device__ __forceinline__ uint64_t splitmix(uint64_t s, uint64_t idx) {
     return mix64(s + (idx + 1) * kGamma);
+}
+
+// ---------------------------------------------------------------------------
+// Level 3: the overflow stash of an iceberg table (Section 2.3 describes a
+// third level; the paper's implementation leaves it out, so the design here
+// is this library's). stash_slots whole keys follow the secondary level's
+// buckets; 0 is EMPTY. A key is placed there only when its primary and both
+// secondary buckets are full, by linear probing from its home position
+// mix64(k ^ stash_key) mod stash_slots; a claim is a 64-bit compare-and-swap
+// EMPTY -> k. Positions never become empty again, so every thread probing
+// for k walks the same filled prefix of k's probe sequence: of concurrent
+// puts of k exactly one claims a position and the others then find k there.
+// ---------------------------------------------------------------------------
+struct StashResult {
+    uint8_t status;  // FOUND / PUT / FULL (puts), FOUND / NOT_FOUND (lookups)
+    uint64_t pos;    // the position that holds k when FOUND or PUT
+};
+
+__device__ __forceinline__ uint64_t *stash_words(const TableArgs &ta) {
+    return ta.lv[1].words + ta.lv[1].nb * kWordsPerBucket;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// find-or-put of k in the stash; the probe sequence is bounded by the
+// stash's size, so the loop always ends
+__device__ __forceinline__ StashResult stash_find_or_put(const TableArgs &ta, uint64_t k,
+                                                         int &fails) {
+    uint64_t *st = stash_words(ta);
+    const uint64_t mask = ta.stash_slots - 1;
+    const uint64_t h = mix64(k ^ ta.stash_key) & mask;
+    for (uint64_t i = 0; i < ta.stash_slots; ++i) {
+        const uint64_t p = (h + i) & mask;
+        uint64_t v = ld_relaxed_u64(st + p);
+        if (v == 0) {
+            const unsigned long long old =
+                atomicCAS(reinterpret_cast<unsigned long long *>(st + p), 0ull,
+                          static_cast<unsigned long long>(k));
+            if (old == 0ull) return {ST_PUT, p};
+            fails++;
+            v = old;
+        }
+        if (v == k) return {ST_FOUND, p};
+    }
+    return {ST_FULL, ~0ull};
+}
+
+// lookup of k in the stash: it ends at k or at the first empty position
+__device__ __forceinline__ StashResult stash_find(const TableArgs &ta, uint64_t k) {
+    const uint64_t *st = stash_words(ta);
+    const uint64_t mask = ta.stash_slots - 1;
+    const uint64_t h = mix64(k ^ ta.stash_key) & mask;
+    for (uint64_t i = 0; i < ta.stash_slots; ++i) {
+        const uint64_t p = (h + i) & mask;
+        const uint64_t v = ld_relaxed_u64(st + p);
+        if (v == k) return {ST_FOUND, p};
+        if (v == 0) break;
+    }
+    return {ST_NOT_FOUND, ~0ull};
 }
 
 // ---------------------------------------------------------------------------

@@ -521,6 +521,17 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
         seen = tile_shfl<T>(seen, cl);
         int cloc = 0;  // the claimed slot's local field in lane cl (slot outputs only)
         if (want_slots) cloc = tile_shfl<T>(lvl == 1 ? f0 : (pick_a ? fa : fb), cl);
+        // level 3: a key whose three buckets are all full goes to the stash
+        // (find-or-put), or is looked up there (lookup: only if both
+        // secondaries are full, as full buckets stay full); the tile's first
+        // lane probes and broadcasts the outcome
+        const bool to_stash = ta.stash_slots && p2 && !bfound &&
+                              (LOOKUP ? (!bea && !beb) : load2 >= B1);
+        StashResult sr{LOOKUP ? ST_NOT_FOUND : ST_FULL, ~0ull};
+        if (to_stash && tl == 0)
+            sr = LOOKUP ? stash_find(ta, cur) : stash_find_or_put(ta, cur, n_fail);
+        sr.status = (uint8_t)tile_shfl<T>((int)sr.status, 0);
+        sr.pos = tile_shfl<T>(sr.pos, 0);
 
         if (act) {
             bool fin = true;
@@ -535,12 +546,15 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
                     if (lvl == 1 && !be0) {
                         fin = false;
                         lvl = 2;
+                    } else if (to_stash) {
+                        st = sr.status;
                     }
                 } else if (lvl == 1 && !be0) {
                     fin = false;
                     lvl = 2;
                 } else if (lvl == 2 && load2 >= B1) {
-                    st = ST_FULL;
+                    st = sr.status;  // FULL, or the stash's answer
+                    if (st == ST_PUT) n_write++;
                 } else if (claimed) {
                     st = ST_PUT;
                     n_write++;
@@ -566,7 +580,9 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
                         // after losing the claim to k itself: the claimed slot
                         const uint64_t B0 = (uint64_t)kWordsPerBucket * FPW0;
                         uint64_t slot = ~0ull;
-                        if (st == ST_FOUND || st == ST_PUT) {
+                        if (to_stash && (st == ST_FOUND || st == ST_PUT)) {
+                            slot = L0.nb * B0 + L1.nb * (uint64_t)B1 + sr.pos;
+                        } else if (st == ST_FOUND || st == ST_PUT) {
                             const bool bym = st == ST_FOUND && bfound;
                             const int ln = bym ? mlane : cl;
                             const int loc = bym ? mloc : cloc;

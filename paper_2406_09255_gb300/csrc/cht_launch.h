@@ -69,6 +69,8 @@ inline int grid_blocks_warp(const void *kern, const LaunchParams &lp, uint64_t n
 cudaError_t launch_values(bool scatter, const uint64_t *slots, uint64_t n, const void *src,
                           void *dst, int value_bytes, uint64_t nslots, int sms,
                           cudaStream_t stream);
+cudaError_t launch_random_claim(void *buf, size_t buf_bytes, uint64_t n_lines, uint64_t seed,
+                                unsigned long long *sink, int sms, cudaStream_t stream);
 cudaError_t launch_random_read(const void *buf, size_t buf_bytes, int block_bytes,
                                uint64_t n_blocks, uint64_t seed, unsigned long long *sink,
                                int sms, cudaStream_t stream);

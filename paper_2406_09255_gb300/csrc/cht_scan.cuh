@@ -27,14 +27,23 @@ __global__ void __launch_bounds__(256)
                 unsigned long long *__restrict__ count) {
     const uint64_t w0 = ta.lv[0].nb * kWordsPerBucket;
     const uint64_t w1 = (kind == 1) ? ta.lv[1].nb * kWordsPerBucket : 0;
-    const uint64_t npairs = (w0 + w1) / 2;  // both levels hold an even word count
+    // the iceberg stash: whole keys after level 1, its storage rounded up
+    // to whole 128-byte lines (the padding words stay zero)
+    const uint64_t ws = (kind == 1) ? (ta.stash_slots + 15) / 16 * 16 : 0;
+    const uint64_t npairs = (w0 + w1 + ws) / 2;  // every region holds an even word count
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < npairs; base += stride) {
         const uint64_t p = base + threadIdx.x;
         uint64_t key[8];
         int cnt = 0;
-        if (p < npairs) {
+        if (p < npairs && 2 * p >= w0 + w1) {
+            // a stash pair: each nonzero word is a stored key
+            const ulonglong2 x = __ldcs(reinterpret_cast<const ulonglong2 *>(
+                ta.lv[1].words + (2 * p - w0)));
+            if (x.x) key[cnt++] = x.x;
+            if (x.y) key[cnt++] = x.y;
+        } else if (p < npairs) {
             const uint64_t wi = 2 * p;
             const int level = wi < w0 ? 0 : 1;
             const uint64_t lw = level ? wi - w0 : wi;
@@ -86,7 +95,8 @@ __global__ void __launch_bounds__(256) k_clear_batch(const BatchDesc *__restrict
         const TableArgs &ta = bd[t].ta;
         ulonglong2 *p = reinterpret_cast<ulonglong2 *>(ta.err);  // header start
         const uint64_t nb = ta.lv[0].nb + ta.lv[1].nb;  // lv[1].nb is 0 for cuckoo
-        const uint64_t n16 = (256 + nb * 128) / 16;
+        const uint64_t stash_bytes = (ta.stash_slots + 15) / 16 * 128;
+        const uint64_t n16 = (256 + nb * 128 + stash_bytes) / 16;
         for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride)
             __stcs(p + i, make_ulonglong2(0ull, 0ull));
     }

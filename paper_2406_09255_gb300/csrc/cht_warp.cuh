@@ -108,7 +108,7 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
         uint64_t k[I];
         uint32_t a0[I];
         E0 e0[I];
-        bool pending[I], lvl2[I];
+        bool pending[I], lvl2[I], lvl3[I];
         uint8_t st[I];
         int it[I];
         uint64_t slot_of[I];  // slot of a FOUND / PUT key (slot outputs only)
@@ -128,7 +128,7 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
             if (!LOOKUP && moves && has) vpre[i] = kv_read(ch.kv->vin, ch.base + pos, ch.kv->vbytes);
             pending[i] = has && valid_key(k[i], ta.w);
             st[i] = pending[i] ? ST_NOT_FOUND : ST_INVALID;
-            lvl2[i] = false;
+            lvl2[i] = lvl3[i] = false;
             it[i] = 0;
             const Quot q = quotient(L0, ta.w, 0, k[i]);
             a0[i] = (uint32_t)q.a;
@@ -275,7 +275,7 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
             more = false;
 #pragma unroll
             for (int i = 0; i < I; ++i) {
-                const bool at2 = pending[i] && lvl2[i];
+                const bool at2 = pending[i] && lvl2[i] && !lvl3[i];
                 pm[i] = __ballot_sync(0xffffffffu, at2) & tmask;
                 more |= pm[i] != 0;
                 aa[i] = ab[i] = 0;
@@ -332,6 +332,14 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                             const int lm = bfound ? __ffs(bfound) - 1 - tbase : 0;
                             y = lm * LF1 + tile_shfl<T>(mval, lm);
                         }
+                        // level 3 holds k only if both secondaries were full
+                        // when it was put, and full buckets stay full
+                        bool both_full = false;
+                        if (ta.stash_slots) {
+                            const uint32_t bea = __ballot_sync(0xffffffffu, live && fa >= 0) & tmask;
+                            const uint32_t beb = __ballot_sync(0xffffffffu, live && fb >= 0) & tmask;
+                            both_full = !bea && !beb;
+                        }
                         if (tl == r) {
                             n_probe += 2;
                             if (bfound) {
@@ -341,7 +349,10 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                                 if (moves && slot_of[i] < ch.kv->nstore)
                                     vpre[i] = kv_read(ch.kv->store, slot_of[i], ch.kv->vbytes);
                             }
-                            pending[i] = false;
+                            if (!bfound && both_full)
+                                lvl3[i] = true;  // the stash, after this pass
+                            else
+                                pending[i] = false;
                         }
                     } else {
                         const uint32_t bea = __ballot_sync(0xffffffffu, live && fa >= 0) & tmask;
@@ -386,8 +397,12 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                                 pending[i] = false;
                                 slot_of[i] = at;
                             } else if (load2 >= B1) {
-                                st[i] = ST_FULL;
-                                pending[i] = false;
+                                if (ta.stash_slots) {
+                                    lvl3[i] = true;  // the stash, after this pass
+                                } else {
+                                    st[i] = ST_FULL;
+                                    pending[i] = false;
+                                }
                             } else if (claimed) {
                                 st[i] = ST_PUT;
                                 pending[i] = false;
@@ -402,6 +417,26 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                                 pending[i] = false;
                                 atomicOr(ta.err, 1u);
                             }
+                        }
+                    }
+                }
+            }
+            // ---- level 3: keys whose three buckets are all full go to the
+            // stash, each lane its own keys (rare: only near capacity)
+            if (ta.stash_slots) {
+                const uint64_t stash_base = L0.nb * B0 + L1.nb * (uint64_t)B1;
+#pragma unroll
+                for (int i = 0; i < I; ++i) {
+                    if (pending[i] && lvl3[i]) {
+                        const StashResult sr = LOOKUP ? stash_find(ta, k[i])
+                                                      : stash_find_or_put(ta, k[i], n_fail);
+                        st[i] = sr.status;
+                        pending[i] = false;
+                        if (sr.status == ST_PUT) n_write++;
+                        if (sr.status == ST_FOUND || sr.status == ST_PUT) {
+                            slot_of[i] = stash_base + sr.pos;
+                            if (LOOKUP && moves && slot_of[i] < ch.kv->nstore)
+                                vpre[i] = kv_read(ch.kv->store, slot_of[i], ch.kv->vbytes);
                         }
                     }
                 }

@@ -128,6 +128,18 @@ def test_random_read_rejects_bad_arguments_without_a_launch(lib):
                              None) == lib.CHT_ERR_INVALID
 
 
+def test_random_claim_rejects_bad_arguments_without_a_launch(lib):
+    L = lib.load()
+    fake = ctypes.c_void_p(1 << 20)
+    sink = ctypes.c_void_p(1 << 21)
+    assert L.cht_random_claim(None, 1 << 20, 10, 0, sink, None) == lib.CHT_ERR_INVALID
+    assert L.cht_random_claim(fake, 3 * 128, 10, 0, sink, None) == lib.CHT_ERR_INVALID
+    assert "power of two" in L.cht_last_error().decode()
+    assert L.cht_random_claim(ctypes.c_void_p((1 << 20) + 64), 1 << 20, 10, 0, sink,
+                              None) == lib.CHT_ERR_INVALID
+    assert L.cht_random_claim(fake, 1 << 20, 0, 0, sink, None) == lib.CHT_OK  # nothing to do
+
+
 def test_value_moves_reject_bad_arguments_without_a_launch(lib):
     L = lib.load()
     fake = ctypes.c_void_p(1 << 20)

@@ -59,11 +59,18 @@ def mirror(t):
     return oracle.Table(c.kind, c.key_bits, c.num_buckets, c.num_buckets_backyard,
                         compact=bool(c.compact), fpw0=c.fields_per_word,
                         fpw1=max(c.fields_per_word_backyard, 1), num_hashes=max(c.num_hashes, 1),
-                        max_chain=max(c.max_chain, 1), seed=c.seed)
+                        max_chain=max(c.max_chain, 1), seed=c.seed, stash=c.stash_slots)
+
+
+def level1_words(t) -> np.ndarray:
+    """The secondary level's words followed by the stash (the oracle's t1)."""
+    if t.cfg.stash_slots:
+        return np.concatenate([words(t, 1), words(t, 2)])
+    return words(t, 1)
 
 
 def dump_into(o, t):
-    o.load_words(words(t, 0), words(t, 1) if t.cfg.kind == 1 else None)
+    o.load_words(words(t, 0), level1_words(t) if t.cfg.kind == 1 else None)
     return o
 
 
@@ -465,6 +472,36 @@ def test_random_read_utility_reads_every_block_size():
                     tot += host[base + k]
                 want ^= np.bitwise_xor.reduce(tot)
         assert (int(sink.item()) & M) == int(want), bb
+
+
+def test_random_claim_utility_claims_the_words_it_should():
+    """cht_random_claim (the put-ceiling measurement) reads line i at
+    splitmix64(seed + i * golden-ratio increment) masked to the line count and
+    compare-and-swaps word (hash >> 40) & 15 of it from the value read to that
+    value + 1. On a zeroed buffer with distinct targets every word ends at 1
+    exactly where a target is, 0 elsewhere."""
+    import ctypes
+    from paper_2406_09255_gb300 import _lib
+    L = _lib.load()
+    nlines, n, seed = 1 << 16, 1 << 10, 5
+
+    def mix(z):
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9))
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB))
+        return z ^ (z >> np.uint64(31))
+
+    with np.errstate(over="ignore"):
+        i = np.arange(n, dtype=np.uint64)
+        h = mix(np.uint64(seed) + i * np.uint64(0x9E3779B97F4A7C15))
+        target = (h & np.uint64(nlines - 1)) * np.uint64(16) + ((h >> np.uint64(40)) & np.uint64(15))
+    assert len(np.unique(target)) == n
+    buf = torch.zeros(nlines * 16, dtype=torch.int64, device=DEV)
+    sink = torch.zeros(1, dtype=torch.int64, device=DEV)
+    _lib.check(L.cht_random_claim(buf.data_ptr(), nlines * 128, n, seed, sink.data_ptr(), None))
+    torch.cuda.synchronize()
+    want = np.zeros(nlines * 16, dtype=np.int64)
+    want[target.astype(np.int64)] = 1
+    assert np.array_equal(buf.cpu().numpy(), want)
 
 
 def test_iceberg_2e22_full_size_stream():
