@@ -7,6 +7,7 @@ unit and the shared headers).
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -59,9 +60,19 @@ def _compile(src: str, extra: list[str], verbose: bool) -> str:
 
 
 def build(verbose: bool = False, extra: list[str] | None = None, jobs: int | None = None) -> str:
-    """Compile every CUDA unit and link libcht.so; returns its path."""
-    extra = list(extra or [])
+    """Compile every CUDA unit and link libcht.so; returns its path. Processes
+    that build at the same time (parallel test workers) take turns."""
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, extra, jobs)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, extra, jobs) -> str:
+    extra = list(extra or [])
     srcs = sources()
     jobs = jobs or min(len(srcs), max(2, os.cpu_count() or 2))
     with cf.ThreadPoolExecutor(jobs) as ex:
