@@ -65,7 +65,8 @@ extern "C" {
 
 /* bytes of the table header at the start of the table storage */
 #define CHT_HEADER_BYTES 256
-/* bytes per bucket: 16 words of 64 bits, one cache line (Section 4.5) */
+/* bytes per bucket by default: 16 words of 64 bits, one cache line
+ * (Section 4.5); see bucket_words for 32- and 64-byte buckets */
 #define CHT_BUCKET_BYTES 128
 
 typedef struct cht_table cht_table; /* opaque host handle */
@@ -132,6 +133,14 @@ typedef struct cht_table cht_table; /* opaque host handle */
  *                       absent key and CHT_FULL only once the key's probe
  *                       sequence holds no free slot. Cuckoo tables must
  *                       leave it 0.
+ * bucket_words          64-bit words per bucket, both levels: 16 (128 bytes,
+ *                       one cache line; 0 selects it), 8 or 4 (64- or
+ *                       32-byte buckets: with 32-bit slots the 16- and 8-slot
+ *                       buckets that Section 5.1 sweeps beside 32). Smaller
+ *                       buckets use tiles of bucket_words / 2 lanes (the tile
+ *                       field must be 0 or that) and offer insert, find,
+ *                       find-or-put and enumerate; slot outputs, key-value
+ *                       calls and fused batches need 16.
  */
 typedef struct cht_config {
     int32_t kind;
@@ -153,6 +162,8 @@ typedef struct cht_config {
     int32_t lookups_in_flight;
     int32_t retry_limit;
     int32_t stash_slots;
+    int32_t bucket_words;
+    int32_t reserved;
 } cht_config;
 
 /* Device counters a table can accumulate into (see cht_set_counters). */
@@ -171,7 +182,7 @@ int cht_resolve_config(const cht_config *cfg, cht_config *out);
 
 /*
  * Bytes of device storage a table of this configuration needs:
- * CHT_HEADER_BYTES + (num_buckets + num_buckets_backyard) * CHT_BUCKET_BYTES
+ * CHT_HEADER_BYTES + (num_buckets + num_buckets_backyard) * 8 * bucket_words
  * (no backyard for cuckoo), plus 8 * stash_slots rounded up to a multiple of
  * CHT_BUCKET_BYTES for an iceberg stash. Returns 0 if the configuration is
  * invalid. Host only.

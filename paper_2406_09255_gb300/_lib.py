@@ -41,10 +41,12 @@ class Config(ctypes.Structure):
         ("lookups_in_flight", ctypes.c_int32),
         ("retry_limit", ctypes.c_int32),
         ("stash_slots", ctypes.c_int32),
+        ("bucket_words", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class Counters(ctypes.Structure):

@@ -124,9 +124,17 @@ int resolve(const cht_config *in, cht_config *out) {
         e = resolve_level(c, 1, c.num_buckets_backyard, c.fields_per_word_backyard);
         if (e) return e;
     }
+    if (c.bucket_words == 0) c.bucket_words = kWordsPerBucket;
+    if (c.bucket_words != 4 && c.bucket_words != 8 && c.bucket_words != 16)
+        return fail(CHT_ERR_INVALID, "bucket_words must be 4, 8 or 16 (got %d)", c.bucket_words);
     // tile 0 stays 0: each operation then uses its own best width
-    if (c.tile != 0 && c.tile != 4 && c.tile != 8 && c.tile != 16)
+    if (c.bucket_words < kWordsPerBucket) {
+        if (c.tile != 0 && c.tile != c.bucket_words / 2)
+            return fail(CHT_ERR_INVALID, "tile must be 0 or %d for %d-word buckets",
+                        c.bucket_words / 2, c.bucket_words);
+    } else if (c.tile != 0 && c.tile != 4 && c.tile != 8 && c.tile != 16) {
         return fail(CHT_ERR_INVALID, "tile must be 4, 8 or 16 (got %d)", c.tile);
+    }
     if (c.items_per_thread == 0) c.items_per_thread = 1;
     if (c.items_per_thread < 1 || c.items_per_thread > 8)
         return fail(CHT_ERR_INVALID, "items_per_thread must be 1..8");
@@ -158,7 +166,7 @@ uint64_t stash_bytes(const cht_config &c) {
 
 size_t table_bytes(const cht_config &c) {
     uint64_t nb = c.num_buckets + (c.kind == CHT_ICEBERG ? c.num_buckets_backyard : 0);
-    return CHT_HEADER_BYTES + (size_t)nb * CHT_BUCKET_BYTES + (size_t)stash_bytes(c);
+    return CHT_HEADER_BYTES + (size_t)nb * 8 * (size_t)c.bucket_words + (size_t)stash_bytes(c);
 }
 
 void fill_level(Level &L, uint64_t *words, uint64_t nb, int key_bits, int fpw, uint64_t seed,
@@ -268,11 +276,12 @@ int cht_create(const cht_config *cfg, void *d_mem, size_t bytes, void *stream, c
     uint64_t *words0 = reinterpret_cast<uint64_t *>(t->mem + CHT_HEADER_BYTES);
     fill_level(a.lv[0], words0, c.num_buckets, c.key_bits, c.fields_per_word, c.seed, 0);
     if (c.kind == CHT_ICEBERG)
-        fill_level(a.lv[1], words0 + c.num_buckets * kWordsPerBucket, c.num_buckets_backyard,
+        fill_level(a.lv[1], words0 + c.num_buckets * (uint64_t)c.bucket_words, c.num_buckets_backyard,
                    c.key_bits, c.fields_per_word_backyard, c.seed, 1);
-    a.w = c.key_bits;
-    a.key_bytes = c.key_bytes;
-    a.H = c.num_hashes;
+    a.w = (int16_t)c.key_bits;
+    a.key_bytes = (int16_t)c.key_bytes;
+    a.H = (int16_t)c.num_hashes;
+    a.wpb = (int16_t)c.bucket_words;
     a.C = c.max_chain;
     a.compact = (int16_t)c.compact;
     a.retry_limit = (int16_t)c.retry_limit;
@@ -333,7 +342,11 @@ int cht_insert(cht_table *t, const void *d_keys, size_t n, uint8_t *d_status,
     if (n == 0) return ok();
     const LaunchParams lp = launch_params(t, stream);
     cudaError_t ce;
-    if (t->cfg.kind == CHT_CUCKOO)
+    if (t->cfg.bucket_words < kWordsPerBucket)
+        ce = launch_small_buckets(t->cfg.kind == CHT_CUCKOO ? kSmallCuckooInsert : kSmallIcebergFop,
+                                  t->cfg.bucket_words, t->cfg.fields_per_word, lp, t->args,
+                                  d_keys, n, d_status, d_dropped);
+    else if (t->cfg.kind == CHT_CUCKOO)
         ce = launch_cuckoo_insert(tile_for(t, kOpCuckooInsert), t->cfg.fields_per_word, lp, t->args, d_keys, n,
                                   d_status, d_dropped);
     else
@@ -348,7 +361,11 @@ int cht_find(const cht_table *t, const void *d_keys, size_t n, uint8_t *d_status
     if (n == 0) return ok();
     const LaunchParams lp = launch_params(t, stream);
     cudaError_t ce;
-    if (t->cfg.kind == CHT_CUCKOO)
+    if (t->cfg.bucket_words < kWordsPerBucket)
+        ce = launch_small_buckets(t->cfg.kind == CHT_CUCKOO ? kSmallCuckooFind : kSmallIcebergFind,
+                                  t->cfg.bucket_words, t->cfg.fields_per_word, lp, t->args,
+                                  d_keys, n, d_status, nullptr);
+    else if (t->cfg.kind == CHT_CUCKOO)
         ce = launch_cuckoo_find(tile_for(t, kOpCuckooFind), t->cfg.fields_per_word, lp, t->args, d_keys, n,
                                 d_status);
     else
@@ -363,6 +380,8 @@ int cht_find_or_put_slots(cht_table *t, const void *d_keys, size_t n, uint8_t *d
     if (e) return e;
     if (t->cfg.kind != CHT_ICEBERG)
         return fail(CHT_ERR_UNSUPPORTED, "slot indices are stable in iceberg tables only");
+    if (t->cfg.bucket_words != kWordsPerBucket)
+        return fail(CHT_ERR_UNSUPPORTED, "slot outputs need 16-word (128-byte) buckets");
     if (!d_slots || (uintptr_t)d_slots % 8) return fail(CHT_ERR_INVALID, "d_slots must be 8-byte aligned");
     if (n == 0) return ok();
     const LaunchParams lp = launch_params(t, stream);
@@ -377,6 +396,8 @@ int cht_find_slots(const cht_table *t, const void *d_keys, size_t n, uint8_t *d_
     if (e) return e;
     if (t->cfg.kind != CHT_ICEBERG)
         return fail(CHT_ERR_UNSUPPORTED, "slot indices are stable in iceberg tables only");
+    if (t->cfg.bucket_words != kWordsPerBucket)
+        return fail(CHT_ERR_UNSUPPORTED, "slot outputs need 16-word (128-byte) buckets");
     if (!d_slots || (uintptr_t)d_slots % 8) return fail(CHT_ERR_INVALID, "d_slots must be 8-byte aligned");
     if (n == 0) return ok();
     const LaunchParams lp = launch_params(t, stream);
@@ -418,6 +439,8 @@ static int kv_check(const cht_table *t, const void *d_keys, size_t n, uint8_t *d
     if (e) return e;
     if (t->cfg.kind != CHT_ICEBERG)
         return fail(CHT_ERR_UNSUPPORTED, "key-value maps need iceberg tables (stable slots)");
+    if (t->cfg.bucket_words != kWordsPerBucket)
+        return fail(CHT_ERR_UNSUPPORTED, "key-value maps need 16-word (128-byte) buckets");
     if (value_bytes != 4 && value_bytes != 8 && value_bytes != 16)
         return fail(CHT_ERR_INVALID, "value_bytes must be 4, 8 or 16");
     if (n && (!values || !store)) return fail(CHT_ERR_INVALID, "null value pointer");
@@ -460,8 +483,12 @@ int cht_find_or_put(cht_table *t, const void *d_keys, size_t n, uint8_t *d_statu
                     "find-or-put is offered by iceberg tables only (cuckoo tables are static)");
     if (n == 0) return ok();
     const LaunchParams lp = launch_params(t, stream);
-    cudaError_t ce = launch_iceberg(tile_for(t, kOpIcebergFop), t->cfg.fields_per_word, false, lp, t->args,
-                                    d_keys, n, d_status);
+    cudaError_t ce =
+        t->cfg.bucket_words < kWordsPerBucket
+            ? launch_small_buckets(kSmallIcebergFop, t->cfg.bucket_words, t->cfg.fields_per_word,
+                                   lp, t->args, d_keys, n, d_status, nullptr)
+            : launch_iceberg(tile_for(t, kOpIcebergFop), t->cfg.fields_per_word, false, lp,
+                             t->args, d_keys, n, d_status);
     return ce == cudaSuccess ? ok() : cuda_fail(ce, "find-or-put kernel launch");
 }
 
@@ -477,7 +504,7 @@ int cht_enumerate(const cht_table *t, void *d_out, size_t cap, uint64_t *d_count
     k_zero_u64<<<1, 32, 0, s>>>(cnt);
     const uint64_t words = (t->cfg.num_buckets +
                             (t->cfg.kind == CHT_ICEBERG ? t->cfg.num_buckets_backyard : 0)) *
-                               kWordsPerBucket +
+                               (uint64_t)t->cfg.bucket_words +
                            stash_bytes(t->cfg) / 8;
     uint64_t blocks = (words / 2 + 255) / 256;
     const uint64_t cap_blocks = (uint64_t)t->sms * 8;
@@ -640,6 +667,11 @@ int cht_batch_create(cht_table *const *tables, const void *const *d_keys, const 
         if (t->cfg.kind != CHT_ICEBERG) {
             delete b;
             return fail(CHT_ERR_UNSUPPORTED, "batch entry %d is not an iceberg table", i);
+        }
+        if (t->cfg.bucket_words != kWordsPerBucket) {
+            delete b;
+            return fail(CHT_ERR_UNSUPPORTED, "batch entry %d has %d-word buckets (fused batches "
+                        "need 16)", i, t->cfg.bucket_words);
         }
         if (i == 0) {
             b->fpw0 = t->cfg.fields_per_word;
@@ -855,6 +887,9 @@ extern "C" int cht_batch_find_or_put_static(cht_table *const *tables, const void
         if (!t) return fail(CHT_ERR_INVALID, "null table at batch entry %d", i);
         if (t->cfg.kind != CHT_ICEBERG)
             return fail(CHT_ERR_UNSUPPORTED, "batch entry %d is not an iceberg table", i);
+        if (t->cfg.bucket_words != kWordsPerBucket)
+            return fail(CHT_ERR_UNSUPPORTED, "batch entry %d has %d-word buckets (fused batches "
+                        "need 16)", i, t->cfg.bucket_words);
         if (t->device != cur)
             return fail(CHT_ERR_INVALID, "batch entry %d is not on the current device", i);
         if (i == 0) {

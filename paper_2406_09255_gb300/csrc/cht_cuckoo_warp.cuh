@@ -20,13 +20,13 @@
 
 namespace cht {
 
-template <int T, int FPW, int I>
+template <int T, int FPW, int I, int WPB = kWordsPerBucket>
 __global__ void __launch_bounds__(256)
     k_cuckoo_insert_warp(TableArgs ta, const void *__restrict__ keys, uint64_t n,
                          uint8_t *__restrict__ status, uint64_t *__restrict__ dropped) {
-    constexpr int W = kWordsPerBucket / T;
+    constexpr int W = WPB / T;
     constexpr int LF = W * FPW;               // fields per lane
-    constexpr int B = kWordsPerBucket * FPW;  // slots per bucket
+    constexpr int B = WPB * FPW;  // slots per bucket
     constexpr uint32_t TM = (T == 32) ? 0xffffffffu : ((1u << T) - 1u);
     using Entry = typename std::conditional<(FPW >= 2), uint32_t, uint64_t>::type;
     const int lane = threadIdx.x & 31;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256)
                     const int sl = r[i] & (T - 1);
                     const uint32_t a = tile_shfl<T>(addr[i], sl);
                     e[i] = tile_shfl<T>(ent[i], sl);
-                    p[i] = const_cast<uint64_t *>(wl) + (uint64_t)a * kWordsPerBucket;
+                    p[i] = const_cast<uint64_t *>(wl) + (uint64_t)a * WPB;
 #pragma unroll
                     for (int x = 0; x < W; ++x) v[i][x] = 0;
                     if (r[i] >= 0) load_relaxed<W>(p[i], v[i]);
@@ -192,13 +192,13 @@ __global__ void __launch_bounds__(256)
 // grid-stride 32-key chunks in order) for the next round, so long eviction
 // chains do not hold other lanes idle.
 // ===========================================================================
-template <int T, int FPW, int Q>
+template <int T, int FPW, int Q, int WPB = kWordsPerBucket>
 __global__ void __launch_bounds__(256, 2)
     k_cuckoo_insert_stream(TableArgs ta, const void *__restrict__ keys, uint64_t n,
                            uint8_t *__restrict__ status, uint64_t *__restrict__ dropped) {
-    constexpr int W = kWordsPerBucket / T;
+    constexpr int W = WPB / T;
     constexpr int LF = W * FPW;               // fields per lane
-    constexpr int B = kWordsPerBucket * FPW;  // slots per bucket
+    constexpr int B = WPB * FPW;  // slots per bucket
     constexpr int QE = Q < T ? Q : T;
     static_assert(T % QE == 0, "slots split evenly into load groups");
     constexpr uint32_t TM = (T == 32) ? 0xffffffffu : ((1u << T) - 1u);
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
             for (int q = 0; q < QE; ++q) {
                 a[q] = tile_shfl<T>(addr, s0 + q);
-                load_relaxed_or_skip<W>((pb >> (s0 + q)) & 1u, wl + (uint64_t)a[q] * kWordsPerBucket,
+                load_relaxed_or_skip<W>((pb >> (s0 + q)) & 1u, wl + (uint64_t)a[q] * WPB,
                                         v[q]);
             }
             // issue: per slot, the acting lane (owner of the first empty slot,
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(256, 2)
                 bes |= (be ? 1u : 0u) << q;
                 old[q] = expd[q] = 0;
                 if (on && tl == actor[q]) {
-                    uint64_t *p = wl + (uint64_t)a[q] * kWordsPerBucket + fidx[q] / FPW;
+                    uint64_t *p = wl + (uint64_t)a[q] * WPB + fidx[q] / FPW;
                     old[q] = field_op_issue<FPW>(!be, p, fidx[q] % FPW,
                                                  pick_word<W>(v[q], fidx[q] / FPW), e, expd[q]);
                 }
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256, 2)
                 bool claimed = false, swap_ok = true;
                 uint64_t evicted = 0;
                 if (on && tl == actor[q]) {
-                    uint64_t *p = wl + (uint64_t)a[q] * kWordsPerBucket + fidx[q] / FPW;
+                    uint64_t *p = wl + (uint64_t)a[q] * WPB + fidx[q] / FPW;
                     if (be) {
                         uint64_t seen = 0;
                         claimed = claim_finish<FPW>(p, fidx[q] % FPW, old[q], expd[q], es[q],

@@ -4,8 +4,10 @@
 // Shuffle over a tile of T threads that owns one bucket) and the field-level
 // compare-and-swap and swap used by Algorithms 1 and 4.
 //
-// Bucket layout: a bucket is 16 little-endian 64-bit words (128 bytes, one
-// cache line, Section 4.5). A level stores fpw fields per word, each
+// Bucket layout: a bucket is WPB little-endian 64-bit words: 16 (128 bytes,
+// one cache line, Section 4.5; the default), or 8 or 4 (64- or 32-byte
+// buckets, the smaller bucket sizes of Section 5.1). A level stores fpw
+// fields per word, each
 // S = 64 / fpw bits wide; slot y is field y % fpw of word y / fpw. The
 // all-zero field is EMPTY. Entries:
 //   cuckoo            (body << 2) | (j + 1)   j = hash index (Section 2.2)
@@ -14,7 +16,7 @@
 // where body is the remainder r_j(k) for compact tables and k itself for
 // whole-key tables.
 //
-// In a tile of T threads lane l owns words [l * W, l * W + W), W = 16 / T,
+// In a tile of T threads lane l owns words [l * W, l * W + W), W = WPB / T,
 // i.e. slots [l * W * fpw, (l + 1) * W * fpw): slot order runs lane by lane,
 // so "the first empty slot" is found with one ballot plus a local scan.
 #pragma once
@@ -24,7 +26,7 @@
 
 namespace cht {
 
-constexpr int kWordsPerBucket = 16;
+constexpr int kWordsPerBucket = 16;  // the default bucket: one 128-byte line
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 
 // status bytes (mirror include/cht.h)
@@ -47,9 +49,10 @@ struct Level {
 // batch descriptor of the fused launch embeds it).
 struct TableArgs {
     Level lv[2];
-    int w;                    // key bits
-    int key_bytes;            // 4 or 8
-    int H;                    // cuckoo hash count
+    int16_t w;                // key bits
+    int16_t key_bytes;        // 4 or 8
+    int16_t H;                // cuckoo hash count
+    int16_t wpb;              // words per bucket: 4, 8 or 16 (32, 64 or 128 bytes)
     int C;                    // cuckoo chain bound
     int16_t compact;          // 1: remainders, 0: whole keys
     int16_t retry_limit;      // iceberg: lost claims a key may retry (0 = built-in bound)
@@ -98,7 +101,7 @@ struct StashResult {
 };
 
 __device__ __forceinline__ uint64_t *stash_words(const TableArgs &ta) {
-    return ta.lv[1].words + ta.lv[1].nb * kWordsPerBucket;
+    return ta.lv[1].words + ta.lv[1].nb * (uint64_t)ta.wpb;
 }
 
 __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {

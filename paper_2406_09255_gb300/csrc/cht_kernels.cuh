@@ -34,13 +34,13 @@ __host__ __device__ inline size_t smem_bytes(int cta_threads, int items) {
 // failed CAS also consumes a step. After C steps the put reports FULL and the
 // key in hand is the dropped one.
 // ===========================================================================
-template <int T, int FPW>
+template <int T, int FPW, int WPB = kWordsPerBucket>
 __global__ void __launch_bounds__(256)
     k_cuckoo_insert(TableArgs ta, const void *__restrict__ keys, uint64_t n,
                     uint8_t *__restrict__ status, uint64_t *__restrict__ dropped, int items) {
-    constexpr int W = kWordsPerBucket / T;
+    constexpr int W = WPB / T;
     constexpr int LF = W * FPW;  // fields per lane
-    constexpr int B = kWordsPerBucket * FPW;
+    constexpr int B = WPB * FPW;
     extern __shared__ uint64_t smem[];
     TileWork<T> tw;
     tw.init(smem, reinterpret_cast<uint8_t *>(smem + (size_t)blockDim.x * items), items, n,
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256)
 
         const Quot qt = quotient(L, ta.w, j, cur);
         const uint64_t entry = ((ta.compact ? qt.r : cur) << 2) | (uint64_t)(j + 1);
-        uint64_t *bp = L.words + qt.a * kWordsPerBucket + tl * W;
+        uint64_t *bp = L.words + qt.a * WPB + tl * W;
         uint64_t v[W] = {};
         if (probe) load_relaxed<W>(bp, v);
         bool m;
@@ -166,11 +166,11 @@ __global__ void __launch_bounds__(256)
 // This form keeps one bucket load in flight per tile; the stream form below
 // is the fast path and this one its plain counterpart.
 // ===========================================================================
-template <int T, int FPW>
+template <int T, int FPW, int WPB = kWordsPerBucket>
 __global__ void __launch_bounds__(256, 6)
     k_cuckoo_find(TableArgs ta, const void *__restrict__ keys, uint64_t n,
                   uint8_t *__restrict__ status) {
-    constexpr int W = kWordsPerBucket / T;
+    constexpr int W = WPB / T;
     // compact entries fit 32 bits when fields are at most 32 bits wide
     using Entry = typename std::conditional<(FPW >= 2), uint32_t, uint64_t>::type;
     const int lane = threadIdx.x & 31;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(256, 6)
             Entry e = tile_shfl<T>(entry, r & (T - 1));
             {
                 const uint32_t a = tile_shfl<T>(addr, r & (T - 1));
-                load_stream_if<W>(r >= 0, words + (uint64_t)a * kWordsPerBucket, v);
+                load_stream_if<W>(r >= 0, words + (uint64_t)a * WPB, v);
             }
             while (__any_sync(0xffffffffu, r >= 0)) {
                 bool m, le;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256, 6)
                 pm &= pm - 1;
                 e = tile_shfl<T>(entry, r & (T - 1));
                 const uint32_t a = tile_shfl<T>(addr, r & (T - 1));
-                load_stream_if<W>(r >= 0, words + (uint64_t)a * kWordsPerBucket, v);
+                load_stream_if<W>(r >= 0, words + (uint64_t)a * WPB, v);
             }
         }
         if (has) status[idx] = st;
@@ -265,11 +265,11 @@ __global__ void __launch_bounds__(256, 6)
 // of use. Probes per key, and so the answers and probe counts, are those of
 // the per-round form.
 // ===========================================================================
-template <int T, int FPW, int Q>
+template <int T, int FPW, int Q, int WPB = kWordsPerBucket>
 __global__ void __launch_bounds__(256, 3)
     k_cuckoo_find_stream(TableArgs ta, const void *__restrict__ keys, uint64_t n,
                          uint8_t *__restrict__ status) {
-    constexpr int W = kWordsPerBucket / T;
+    constexpr int W = WPB / T;
     constexpr int QE = Q < T ? Q : T;
     static_assert(T % QE == 0, "slots split evenly into load groups");
     using Entry = typename std::conditional<(FPW >= 2), uint32_t, uint64_t>::type;
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(256, 3)
             for (int q = 0; q < QE; ++q) {
                 const uint32_t a = tile_shfl<T>(addr, s0 + q);
                 load_stream_or_skip<W>((pb >> (s0 + q)) & 1u,
-                                       words + (uint64_t)a * kWordsPerBucket, v[q]);
+                                       words + (uint64_t)a * WPB, v[q]);
             }
 #pragma unroll
             for (int q = 0; q < QE; ++q) {
@@ -414,9 +414,9 @@ struct BatchDesc {
     uint8_t *status;
 };
 
-template <int T, int FPW0, bool LOOKUP, class Work>
+template <int T, int FPW0, bool LOOKUP, class Work, int WPB = kWordsPerBucket>
 __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr) {
-    constexpr int W = kWordsPerBucket / T;
+    constexpr int W = WPB / T;
     const int tl = threadIdx.x & (T - 1);
     uint64_t cur = 0;
     int lvl = 1, it = 0;
@@ -432,7 +432,7 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
         const Level &L1 = ta.lv[1];
         const int FPW1 = L1.fpw;
         const int LF1 = W * FPW1;
-        const int B1 = kWordsPerBucket * FPW1;
+        const int B1 = WPB * FPW1;
         const bool act = !tw.done;
         if (act && fresh) {
             cur = tw.s_keys[tw.q];
@@ -450,9 +450,9 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
         const uint64_t e0 = ((ta.compact ? q0.r : cur) << 1) | 1ull;
         const uint64_t ea = ((ta.compact ? qa.r : cur) << 2) | 1ull;
         const uint64_t eb = ((ta.compact ? qb.r : cur) << 2) | 2ull;
-        uint64_t *p0 = L0.words + q0.a * kWordsPerBucket + tl * W;
-        uint64_t *pa = L1.words + qa.a * kWordsPerBucket + tl * W;
-        uint64_t *pb = L1.words + qb.a * kWordsPerBucket + tl * W;
+        uint64_t *p0 = L0.words + q0.a * WPB + tl * W;
+        uint64_t *pa = L1.words + qa.a * WPB + tl * W;
+        uint64_t *pb = L1.words + qb.a * WPB + tl * W;
         uint64_t v0[W] = {}, va[W] = {}, vb[W] = {};
         if (p1) load_relaxed<W>(p0, v0);
         if (p2) {
@@ -560,7 +560,7 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
                     n_write++;
                 } else {
                     const uint64_t mine = (lvl == 1) ? e0 : (pick_a ? ea : eb);
-                    const int max_iter = iceberg_retry_bound(ta, kWordsPerBucket * FPW0, B1);
+                    const int max_iter = iceberg_retry_bound(ta, WPB * FPW0, B1);
                     if (seen == mine) {
                         st = ST_FOUND;  // another thread inserted k first
                     } else if (++it > max_iter) {
@@ -578,7 +578,7 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
                     if (want_slots) {
                         // FOUND by a match: the matching slot; PUT, or FOUND
                         // after losing the claim to k itself: the claimed slot
-                        const uint64_t B0 = (uint64_t)kWordsPerBucket * FPW0;
+                        const uint64_t B0 = (uint64_t)WPB * FPW0;
                         uint64_t slot = ~0ull;
                         if (to_stash && (st == ST_FOUND || st == ST_PUT)) {
                             slot = L0.nb * B0 + L1.nb * (uint64_t)B1 + sr.pos;
@@ -613,7 +613,7 @@ __device__ __forceinline__ void iceberg_engine(Work &tw, unsigned long long *ctr
     }
 }
 
-template <int T, int FPW0, bool LOOKUP>
+template <int T, int FPW0, bool LOOKUP, int WPB = kWordsPerBucket>
 __global__ void __launch_bounds__(256)
     k_iceberg(TableArgs ta, const void *__restrict__ keys, uint64_t n,
               uint8_t *__restrict__ status, uint64_t *__restrict__ slots, KVArgs kv, int items) {
@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(256)
     tw.status = status;
     tw.slots = slots;
     tw.kv = &kv;
-    iceberg_engine<T, FPW0, LOOKUP>(tw, ta.ctr);
+    iceberg_engine<T, FPW0, LOOKUP, SingleWork<T>, WPB>(tw, ta.ctr);
 }
 
 }  // namespace cht

@@ -93,6 +93,13 @@ cudaError_t launch_iceberg_warp_slots(int T, int fpw0, bool lookup, const Launch
                                       const TableArgs &ta, const void *keys, uint64_t n,
                                       uint8_t *status, uint64_t *slots, const KVArgs &kv);
 
+// tables with 32- or 64-byte buckets (wpb = 4 or 8 words): one launcher for
+// the four operations, tiles of wpb / 2 lanes
+enum SmallOp { kSmallCuckooInsert, kSmallCuckooFind, kSmallIcebergFop, kSmallIcebergFind };
+cudaError_t launch_small_buckets(int op, int wpb, int fpw, const LaunchParams &lp,
+                                 const TableArgs &ta, const void *keys, uint64_t n,
+                                 uint8_t *status, uint64_t *dropped);
+
 struct BatchDesc;
 // launch shape of the allocation-free fused find-or-put
 constexpr int kStaticBatchTile = 4;

@@ -25,8 +25,8 @@ __device__ __forceinline__ uint64_t decode_entry(const TableArgs &ta, int kind, 
 __global__ void __launch_bounds__(256)
     k_enumerate(TableArgs ta, int kind, void *__restrict__ out, uint64_t cap,
                 unsigned long long *__restrict__ count) {
-    const uint64_t w0 = ta.lv[0].nb * kWordsPerBucket;
-    const uint64_t w1 = (kind == 1) ? ta.lv[1].nb * kWordsPerBucket : 0;
+    const uint64_t w0 = ta.lv[0].nb * (uint64_t)ta.wpb;
+    const uint64_t w1 = (kind == 1) ? ta.lv[1].nb * (uint64_t)ta.wpb : 0;
     // the iceberg stash: whole keys after level 1, its storage rounded up
     // to whole 128-byte lines (the padding words stay zero)
     const uint64_t ws = (kind == 1) ? (ta.stash_slots + 15) / 16 * 16 : 0;
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256)
             const uint64_t lw = level ? wi - w0 : wi;
             const uint64_t *src = ta.lv[level].words + lw;
             const ulonglong2 x = __ldcs(reinterpret_cast<const ulonglong2 *>(src));
-            const uint64_t a = lw / kWordsPerBucket;
+            const uint64_t a = lw / (uint64_t)ta.wpb;
             const int fpw = ta.lv[level].fpw;
             const int S = 64 / fpw;
             const uint64_t M = (S >= 64) ? ~0ull : ((1ull << S) - 1ull);
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_clear_batch(const BatchDesc *__restrict
         ulonglong2 *p = reinterpret_cast<ulonglong2 *>(ta.err);  // header start
         const uint64_t nb = ta.lv[0].nb + ta.lv[1].nb;  // lv[1].nb is 0 for cuckoo
         const uint64_t stash_bytes = (ta.stash_slots + 15) / 16 * 128;
-        const uint64_t n16 = (256 + nb * 128 + stash_bytes) / 16;
+        const uint64_t n16 = (256 + nb * 8 * (uint64_t)ta.wpb + stash_bytes) / 16;
         for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride)
             __stcs(p + i, make_ulonglong2(0ull, 0ull));
     }

@@ -78,9 +78,10 @@ struct BatchSource {
 // SLOTS: also write each FOUND / PUT key's slot index to the chunk's slots
 // array (the key-value extension); a separate instantiation, so that plain
 // runs pay nothing for it
-template <int T, int FPW0, int I, bool LOOKUP, class Src, bool SLOTS = false>
+template <int T, int FPW0, int I, bool LOOKUP, class Src, bool SLOTS = false,
+          int WPB = kWordsPerBucket>
 __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long *ctr) {
-    constexpr int W = kWordsPerBucket / T;
+    constexpr int W = WPB / T;
     constexpr uint32_t TM = (T == 32) ? 0xffffffffu : ((1u << T) - 1u);
     using E0 = typename std::conditional<(FPW0 >= 2), uint32_t, uint64_t>::type;
     const int lane = threadIdx.x & 31;
@@ -100,8 +101,8 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
         const Level &L1 = ta.lv[1];
         const int FPW1 = L1.fpw;
         const int LF1 = W * FPW1;
-        const int B1 = kWordsPerBucket * FPW1;
-        const int max_iter = iceberg_retry_bound(ta, kWordsPerBucket * FPW0, B1);
+        const int B1 = WPB * FPW1;
+        const int max_iter = iceberg_retry_bound(ta, WPB * FPW0, B1);
         const uint64_t *w0 = L0.words + tl * W;
         const uint64_t *w1 = L1.words + tl * W;
 
@@ -117,7 +118,7 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
         KVal vpre[I];
         const bool moves = SLOTS && ch.kv->store != nullptr;
         constexpr bool want_slots = SLOTS;
-        const uint64_t B0 = (uint64_t)kWordsPerBucket * FPW0;
+        const uint64_t B0 = (uint64_t)WPB * FPW0;
 #pragma unroll
         for (int i = 0; i < I; ++i) {
             slot_of[i] = ~0ull;
@@ -159,7 +160,7 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                     const int sl = r[i] & (T - 1);
                     const uint32_t a = tile_shfl<T>(a0[i], sl);
                     e[i] = tile_shfl<T>(e0[i], sl);
-                    p[i] = w0 + (uint64_t)a * kWordsPerBucket;
+                    p[i] = w0 + (uint64_t)a * WPB;
 #pragma unroll
                     for (int x = 0; x < W; ++x) v[i][x] = 0;
                     if (r[i] >= 0) load_relaxed<W>(p[i], v[i]);
@@ -300,8 +301,8 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                     const int sl = r & (T - 1);
                     const uint32_t xa = tile_shfl<T>(aa[i], sl), xb = tile_shfl<T>(ab[i], sl);
                     const uint64_t ya = tile_shfl<T>(ea[i], sl), yb = tile_shfl<T>(eb[i], sl);
-                    uint64_t *pa = const_cast<uint64_t *>(w1) + (uint64_t)xa * kWordsPerBucket;
-                    uint64_t *pb = const_cast<uint64_t *>(w1) + (uint64_t)xb * kWordsPerBucket;
+                    uint64_t *pa = const_cast<uint64_t *>(w1) + (uint64_t)xa * WPB;
+                    uint64_t *pb = const_cast<uint64_t *>(w1) + (uint64_t)xb * WPB;
                     uint64_t va[W] = {}, vb[W] = {};
                     if (live) {
                         load_relaxed<W>(pa, va);
@@ -473,12 +474,12 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
 
 // five blocks per SM (48 registers): measured 5-8 % faster than four blocks
 // with fewer spills, and faster than six blocks with more
-template <int T, int FPW0, int I, bool LOOKUP>
+template <int T, int FPW0, int I, bool LOOKUP, int WPB = kWordsPerBucket>
 __global__ void __launch_bounds__(256, 5)
     k_iceberg_warp(TableArgs ta, const void *__restrict__ keys, uint64_t n,
                    uint8_t *__restrict__ status) {
     SingleSource src{&ta, keys, status, nullptr, nullptr, n, (uint64_t)32 * I};
-    iceberg_warp<T, FPW0, I, LOOKUP, SingleSource, false>(src, ta.ctr);
+    iceberg_warp<T, FPW0, I, LOOKUP, SingleSource, false, WPB>(src, ta.ctr);
 }
 
 // with slot outputs and value moves (one key per lane); held to 64 registers

@@ -18,7 +18,8 @@ __all__ = ["Table", "CUCKOO", "ICEBERG", "resolve_config", "table_bytes"]
 def _make_config(kind, key_bits, num_buckets, num_buckets_backyard=0, *, compact=True,
                  key_bytes=8, fields_per_word=0, fields_per_word_backyard=0, num_hashes=0,
                  max_chain=0, seed=0, tile=0, items_per_thread=0, cta_threads=0, max_ctas=0,
-                 max_tiles=0, lookups_in_flight=0, retry_limit=0, stash_slots=0) -> Config:
+                 max_tiles=0, lookups_in_flight=0, retry_limit=0, stash_slots=0,
+                 bucket_words=0) -> Config:
     c = Config()
     c.kind, c.compact, c.key_bits, c.key_bytes = kind, int(compact), key_bits, key_bytes
     c.num_buckets, c.num_buckets_backyard = num_buckets, num_buckets_backyard
@@ -30,6 +31,7 @@ def _make_config(kind, key_bits, num_buckets, num_buckets_backyard=0, *, compact
     c.lookups_in_flight = lookups_in_flight
     c.retry_limit = retry_limit
     c.stash_slots = stash_slots
+    c.bucket_words = bucket_words
     return c
 
 
@@ -100,9 +102,10 @@ class Table:
     @property
     def slots(self) -> int:
         c = self.cfg
-        n = c.num_buckets * 16 * c.fields_per_word
+        wpb = c.bucket_words
+        n = c.num_buckets * wpb * c.fields_per_word
         if c.kind == ICEBERG:
-            n += c.num_buckets_backyard * 16 * c.fields_per_word_backyard + c.stash_slots
+            n += c.num_buckets_backyard * wpb * c.fields_per_word_backyard + c.stash_slots
         return n
 
     def clear(self, stream=None):
@@ -221,10 +224,10 @@ class Table:
         (level 2: the iceberg stash's slots)."""
         c = self.cfg
         w = self.storage[_lib.HEADER_BYTES:].view(torch.int64)
-        n0 = c.num_buckets * 16
+        n0 = c.num_buckets * c.bucket_words
         if level == 0:
             return w[:n0]
-        n1 = c.num_buckets_backyard * 16
+        n1 = c.num_buckets_backyard * c.bucket_words
         if level == 1:
             return w[n0: n0 + n1]
         # level 2: the iceberg stash (whole keys, 0 = empty)

@@ -35,8 +35,9 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_binding_struct_matches_header_layout(lib):
-    # 4 ints, 2 u64, 4 ints, u64, 6 ints, retry_limit and one reserved int
-    assert ctypes.sizeof(lib.Config) == 4 * 4 + 16 + 4 * 4 + 8 + 6 * 4 + 8
+    # 4 ints, 2 u64, 4 ints, u64, 6 launch ints, retry_limit, stash_slots,
+    # bucket_words and one reserved int
+    assert ctypes.sizeof(lib.Config) == 4 * 4 + 16 + 4 * 4 + 8 + 6 * 4 + 16
     assert ctypes.sizeof(lib.Counters) == 32
 
 
@@ -103,11 +104,35 @@ def test_bit_budget_section_5_1(lib):
      "retry_limit"),
     (dict(kind=1, key_bits=32, num_buckets=16, num_buckets_backyard=2, retry_limit=40000),
      "retry_limit"),
+    (dict(kind=0, key_bits=32, num_buckets=16, stash_slots=8), "stash"),
+    (dict(kind=1, key_bits=32, num_buckets=16, num_buckets_backyard=2, stash_slots=12), "stash"),
+    (dict(kind=0, key_bits=32, num_buckets=16, bucket_words=6), "bucket_words"),
+    (dict(kind=0, key_bits=32, num_buckets=16, bucket_words=8, tile=8), "tile must be 0 or 4"),
 ])
 def test_invalid_configs_rejected_with_message(lib, kw, frag):
     code, _ = _resolve(lib, **kw)
     assert code == lib.CHT_ERR_INVALID
     assert frag in lib.load().cht_last_error().decode()
+
+
+def test_storage_sizes_of_stash_and_bucket_widths(lib):
+    L = lib.load()
+    from paper_2406_09255_gb300.table import _make_config
+    c = _make_config(kind=1, key_bits=32, num_buckets=1 << 10, num_buckets_backyard=1 << 7)
+    base = L.cht_table_bytes(ctypes.byref(c))
+    assert base == 256 + ((1 << 10) + (1 << 7)) * 128
+    # the stash: 8 bytes a slot, rounded up to 128-byte lines
+    for slots, extra in ((2, 128), (16, 128), (32, 256), (1 << 20, 8 << 20)):
+        c = _make_config(kind=1, key_bits=32, num_buckets=1 << 10, num_buckets_backyard=1 << 7,
+                         stash_slots=slots)
+        assert L.cht_table_bytes(ctypes.byref(c)) == base + extra
+    for wpb in (4, 8):
+        c = _make_config(kind=0, key_bits=32, num_buckets=1 << 10, bucket_words=wpb)
+        assert L.cht_table_bytes(ctypes.byref(c)) == 256 + (1 << 10) * 8 * wpb
+        code, r = _resolve(lib, kind=0, key_bits=32, num_buckets=1 << 10, bucket_words=wpb)
+        assert code == 0 and r.bucket_words == wpb
+    code, r = _resolve(lib, kind=0, key_bits=32, num_buckets=1 << 10)
+    assert code == 0 and r.bucket_words == 16
 
 
 def test_version(lib):

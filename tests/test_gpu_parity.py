@@ -59,7 +59,8 @@ def mirror(t):
     return oracle.Table(c.kind, c.key_bits, c.num_buckets, c.num_buckets_backyard,
                         compact=bool(c.compact), fpw0=c.fields_per_word,
                         fpw1=max(c.fields_per_word_backyard, 1), num_hashes=max(c.num_hashes, 1),
-                        max_chain=max(c.max_chain, 1), seed=c.seed, stash=c.stash_slots)
+                        max_chain=max(c.max_chain, 1), seed=c.seed, stash=c.stash_slots,
+                        wpb=c.bucket_words)
 
 
 def level1_words(t) -> np.ndarray:

@@ -32,9 +32,9 @@ def built():
 
 GEOMS = [
     # (key_bits, key_bytes, log2 primary, log2 backyard, fpw0, fpw1, stash slots)
-    (32, 4, 3, 1, 2, 2, 64),
+    (32, 4, 3, 1, 2, 1, 64),
     (40, 8, 3, 1, 1, 1, 32),
-    (19, 4, 3, 1, 4, 2, 128),
+    (18, 4, 3, 1, 4, 2, 128),
 ]
 
 
@@ -110,7 +110,7 @@ def test_concurrent_past_the_stash():
     P = cht()
     w = 32
     t = P.Table(P.ICEBERG, w, 1 << 3, 1 << 1, key_bytes=4, fields_per_word=2,
-                fields_per_word_backyard=2, stash_slots=16, seed=9)
+                stash_slots=16, seed=9)
     fresh, keys = _stream(t, w, 1.4, 99)
     kn = keys.numpy().astype(np.uint64)
     st = t.find_or_put(dev_keys(keys, 4)).cpu().numpy()
