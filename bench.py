@@ -752,6 +752,75 @@ def run_iceberg_variants(args, dev):
     return out
 
 
+def run_bucket_sizes(args, dev):
+    """Bucket sizes of 8, 16 and 32 slots (Section 5.1's sweep): compact
+    cuckoo (2^27 slots, H = 3) and compact iceberg (2^27 primary + 2^24
+    secondary slots) tables of 32-bit slots (two per word) in buckets of 32,
+    64 and 128 bytes at equal slot counts, 37-bit keys (the paper's key
+    range). Unique keys are put to fills 0.5 / 0.7 / 0.8 / 0.9 / 0.95 (cuckoo
+    puts, iceberg find-or-puts), each step timed with the FULL count it
+    returned, and after each fill 2^26 lookups at 50 % hit are timed."""
+    from paper_2406_09255_gb300 import CUCKOO, ICEBERG, Table
+    from paper_2406_09255_gb300 import workloads as W
+    w, seed, nq = 37, W.SEED_BASE + 8, 1 << 26
+    fills = (0.5, 0.7, 0.8, 0.9, 0.95)
+
+    def ev_ms(fn):
+        a, b = _events()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    results = {}
+    for kind in ("cuckoo", "iceberg"):
+        for wpb in (4, 8, 16):
+            slots_per_bucket = 2 * wpb
+            if kind == "cuckoo":
+                t = Table(CUCKOO, w, (1 << 27) // slots_per_bucket, fields_per_word=2,
+                          bucket_words=wpb, seed=8000, device=dev)
+            else:
+                t = Table(ICEBERG, w, (1 << 27) // slots_per_bucket,
+                          (1 << 24) // slots_per_bucket, fields_per_word=2,
+                          fields_per_word_backyard=2, bucket_words=wpb, seed=8000, device=dev)
+            bounds = [0] + [int(f * t.slots) for f in fills]
+            keys = W.unique_keys(0, bounds[-1], w, seed, device=dev)
+            st = torch.empty(bounds[-1], dtype=torch.uint8, device=dev)
+            fst = torch.empty(nq, dtype=torch.uint8, device=dev)
+            rows = {f: {"put": [], "find": [], "full": 0} for f in fills}
+            for rep in range(max(1, args.steps)):
+                t.clear()
+                torch.cuda.synchronize()
+                for i, f in enumerate(fills):
+                    lo, hi = bounds[i], bounds[i + 1]
+                    op = t.insert if kind == "cuckoo" else t.find_or_put
+                    ms = ev_ms(lambda: op(keys[lo:hi], status=st[lo:hi]))
+                    rows[f]["put"].append((hi - lo) / ms / 1e3)
+                    rows[f]["full"] = int((st[lo:hi] == 3).sum().item())
+                    q, _ = W.find_queries(hi, nq, 0.5, w, seed, bounds[-1], device=dev,
+                                          shuffle_seed=seed + i)
+                    ms = ev_ms(lambda: t.find(q, status=fst))
+                    rows[f]["find"].append(nq / ms / 1e3)
+                    del q
+            first_full = next((f for f in fills if rows[f]["full"]), None)
+            results[f"{kind}_{slots_per_bucket}_slots"] = {
+                "bucket_bytes": 8 * wpb, "slots": t.slots,
+                "put_mops": {str(f): statistics.median(rows[f]["put"]) for f in fills},
+                "find50_mops": {str(f): statistics.median(rows[f]["find"]) for f in fills},
+                "full_puts": {str(f): rows[f]["full"] for f in fills},
+                "first_fill_with_full": first_full}
+            del t, keys, st, fst
+            torch.cuda.empty_cache()
+    return {"metric": "Mops/s put and find vs fill by bucket size (8, 16, 32 slots of 32 bits)",
+            "value": results["cuckoo_32_slots"]["find50_mops"]["0.9"], "unit": "Mops/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "bucket_sizes: 37-bit keys, 32-bit slots; cuckoo 2^27 slots "
+                                   "(H=3), iceberg 2^27 + 2^24 slots; buckets of 32/64/128 B; "
+                                   "fills 0.5/0.7/0.8/0.9/0.95; 2^26 lookups at 50% hit"},
+            "results": results}
+
+
 def run_kv(args, dev):
     """Key-value extension on the 2^22 + 2^19 compact iceberg table (48-bit
     keys, 8-byte values): put = find-or-put with slots + value scatter, get =
@@ -962,7 +1031,8 @@ def extra_configs(args, dev, compact_phases):
     """The other configurations, after the headline and outside its timed
     region, each with its own clock samples: the same library's whole-key
     cuckoo tables (equal memory, equal slots), the iceberg find-or-put
-    stream, the 256-table fused batch and the served request loop."""
+    stream, the 256-table fused batch, the bucket-size sweep and the served
+    request loop."""
     import argparse as _ap
     res = {}
 
@@ -1001,6 +1071,7 @@ def extra_configs(args, dev, compact_phases):
     res["compact_over_whole_key"] = cmp_rows
     section("iceberg_stream", lambda: run_iceberg_stream(_ap.Namespace(steps=3, warmup=1), dev))
     section("batch256", lambda: run_batch256(_ap.Namespace(steps=5, warmup=2), dev))
+    section("bucket_sizes", lambda: run_bucket_sizes(_ap.Namespace(steps=2, warmup=1), dev))
     section("served", lambda: run_served(few, dev))
     return res
 
@@ -1013,7 +1084,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     others = {"iceberg_stream": run_iceberg_stream, "batch256": run_batch256,
               "served": run_served, "iceberg_variants": run_iceberg_variants,
-              "random_read": run_random_read, "kv": run_kv}
+              "random_read": run_random_read, "kv": run_kv, "bucket_sizes": run_bucket_sizes}
     ap.add_argument("--workload", default="cuckoo_2e24", choices=sorted(WORKLOADS) + sorted(others))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
