@@ -1,12 +1,25 @@
-"""Autotuner for the launch shape of table operations and fused batches.
+"""Autotuner for the launch shape of table operations and fused batches, and
+for the slot packing of new tables.
 
 For a given operation it times every candidate (threads per bucket tile,
 items per thread), restoring the tables' contents before each trial so that
 every candidate sees the same state, and keeps the fastest. Results are cached
 in a JSON file (CHT_TUNE_CACHE, default ~/.cache/cht_tune.json) under a key
-built from the device, the operation, the table kind, the primary packing and
-the size class (log2 of the largest primary bucket count), so later runs of
-the same shape skip the sweep.
+built from the device, the operation, the table kind, the packing of both
+levels and the size class (log2 of the largest primary bucket count), so
+later runs of the same shape skip the sweep.
+
+Tiles are 4, 8 or 16 lanes: a lane owns whole 64-bit words of the bucket
+(slots are fields of a word and a claim is a compare-and-swap of one word's
+field), and a 16-word bucket split over 32 lanes would leave a lane half a
+word. Items per lane are 1, 2 or 4, the counts the kernels are built for
+(larger settings run the 4-key form).
+
+tune_packing chooses, for a table about to be created, between the densest
+packing that holds its entries and the next wider one (fewer, wider fields
+per word: 16- or 32-bit fields take a native compare-and-swap of their own
+width, 21-bit fields a retried 64-bit one), by timing the operation on a
+fresh table of each packing with the same bucket counts.
 """
 from __future__ import annotations
 
@@ -19,7 +32,7 @@ import threading
 import torch
 
 TILES = (4, 8, 16)
-ITEMS = (1, 2, 4, 8)
+ITEMS = (1, 2, 4)
 
 _lock = threading.Lock()
 
@@ -53,7 +66,30 @@ def shape_key(op: str, tables) -> str:
     c = tables[0].cfg
     size_class = max(int(math.log2(max(t.cfg.num_buckets, 1))) for t in tables)
     dev = torch.cuda.get_device_name(tables[0].device)
-    return f"{dev}|{op}|kind{c.kind}|compact{c.compact}|fpw{c.fields_per_word}|lg{size_class}|n{len(tables)}"
+    return (f"{dev}|{op}|kind{c.kind}|compact{c.compact}|fpw{c.fields_per_word}"
+            f"/{c.fields_per_word_backyard}|wpb{c.bucket_words}|lg{size_class}|n{len(tables)}")
+
+
+def _fits(body_bits: int, tag_bits: int, fpw: int) -> bool:
+    return body_bits + tag_bits <= 64 // fpw
+
+
+def packing_candidates(kind: int, key_bits: int, num_buckets: int,
+                       num_buckets_backyard: int = 0, compact: bool = True) -> list:
+    """(fields_per_word, fields_per_word_backyard) pairs tune_packing tries:
+    per level the densest packing whose fields hold an entry (remainder of
+    key_bits - log2(buckets) bits, or the whole key, plus the tag: 2 bits
+    for cuckoo and iceberg secondary entries, 1 for iceberg primary ones)
+    and the next wider one, when there is one."""
+    def level(nb: int, tag: int) -> list:
+        if not compact:
+            return [1]
+        body = key_bits - max(0, math.ceil(math.log2(max(nb, 1))))
+        dense = max(f for f in (1, 2, 3, 4) if _fits(body, tag, f))
+        return [dense] if dense == 1 else [dense, dense - 1]
+    if kind == 0:
+        return [(f, 0) for f in level(num_buckets, 2)]
+    return [(f0, f1) for f0 in level(num_buckets, 1) for f1 in level(num_buckets_backyard, 2)]
 
 
 def _time(fn, reps: int) -> float:
@@ -171,3 +207,53 @@ def tune_table(table, op: str, keys: torch.Tensor, reps: int = 3, use_cache: boo
         _store(key, out)
     return dict(out, cached=False,
                 sweep=[{"tile": T, "items": I, "in_flight": P, "ms": m} for m, T, I, P in results])
+
+
+def tune_packing(kind: int, key_bits: int, num_buckets: int, num_buckets_backyard: int,
+                 keys: torch.Tensor, op: str, reps: int = 3, use_cache: bool = True,
+                 **table_kw) -> dict:
+    """Choose the slot packing of a new table by measurement.
+
+    Every candidate of packing_candidates gets a fresh table with the given
+    bucket counts, and `op` ("insert", "find_or_put") over `keys` is timed
+    on it from empty, reps times. A candidate whose run reports more FULL
+    keys than the densest packing's is dropped (a wider packing holds fewer
+    slots). Returns {"fields_per_word", "fields_per_word_backyard", "ms",
+    "sweep", "cached"}; the choice is cached under the operation, kind, key
+    width, bucket counts and key count."""
+    from . import Table
+    dev = keys.device
+    lg0 = int(math.log2(max(num_buckets, 1)))
+    lg1 = int(math.log2(max(num_buckets_backyard, 1))) if num_buckets_backyard else 0
+    key = (f"{torch.cuda.get_device_name(dev)}|packing|{op}|kind{kind}|w{key_bits}|lg{lg0}/{lg1}"
+           f"|n{int(math.log2(max(keys.numel(), 1)))}")
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit:
+            return dict(hit, cached=True)
+    results = []
+    full_dense = None
+    for f0, f1 in packing_candidates(kind, key_bits, num_buckets, num_buckets_backyard,
+                                     table_kw.get("compact", True)):
+        t = Table(kind, key_bits, num_buckets, num_buckets_backyard, fields_per_word=f0,
+                  fields_per_word_backyard=f1, device=dev, **table_kw)
+        status = torch.empty(keys.numel(), dtype=torch.uint8, device=dev)
+        fn = getattr(t, op)
+        ms = []
+        for _ in range(reps):
+            t.clear()
+            torch.cuda.synchronize()
+            ms.append(_time(lambda: fn(keys, status=status), 1))
+        full = int((status == 3).sum().item())
+        if full_dense is None:
+            full_dense = full
+        results.append({"fields_per_word": f0, "fields_per_word_backyard": f1,
+                        "ms": statistics.median(ms), "full": full})
+        del t
+    ok = [r for r in results if r["full"] <= full_dense]
+    best = min(ok, key=lambda r: r["ms"])
+    out = {"fields_per_word": best["fields_per_word"],
+           "fields_per_word_backyard": best["fields_per_word_backyard"], "ms": best["ms"]}
+    if use_cache:
+        _store(key, out)
+    return dict(out, cached=False, sweep=results)

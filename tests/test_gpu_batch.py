@@ -184,3 +184,33 @@ def test_table_tuner_sweeps_loads_in_flight(tmp_path, monkeypatch):
     assert (st == P().PUT).all() and t.enumerate()[1] == n
     r2 = tune_table(t, "insert", keys, reps=1)
     assert r2["cached"] and r2["in_flight"] == r["in_flight"]
+
+
+def test_packing_tuner_times_densest_and_wider(tmp_path, monkeypatch):
+    """tune_packing times find-or-put on a fresh table of each candidate
+    packing (densest, and one step wider per level) and returns one; a table
+    built with the choice meets the find-or-put contract against the
+    oracle."""
+    monkeypatch.setenv("CHT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    import oracle
+    from paper_2406_09255_gb300.tune import packing_candidates, tune_packing
+    w, nb0, nb1 = 48, 1 << 12, 1 << 9
+    keys = W.unique_keys(0, 40000, w, 515)
+    keys = torch.cat([keys, keys[:10000]]).to(DEV)
+    r = tune_packing(1, w, nb0, nb1, keys, "find_or_put", reps=1, seed=5)
+    cands = packing_candidates(1, w, nb0, nb1)
+    assert len(r["sweep"]) == len(cands) == 4 and not r["cached"]
+    assert (r["fields_per_word"], r["fields_per_word_backyard"]) in cands
+    t = P().Table(P().ICEBERG, w, nb0, nb1, fields_per_word=r["fields_per_word"],
+                  fields_per_word_backyard=r["fields_per_word_backyard"], seed=5)
+    st = t.find_or_put(keys).cpu().numpy()
+    kn = keys.cpu().numpy().view(np.uint64)
+    o = oracle.Table(oracle.ICEBERG, w, nb0, nb1, fpw0=t.cfg.fields_per_word,
+                     fpw1=t.cfg.fields_per_word_backyard, seed=t.cfg.seed)
+    ost = o.insert(kn)
+    assert (ost != oracle.FULL).all()
+    uniq, inv = np.unique(kn, return_inverse=True)
+    puts = np.bincount(inv, weights=(st == P().PUT), minlength=len(uniq))
+    assert (puts == 1).all()
+    r2 = tune_packing(1, w, nb0, nb1, keys, "find_or_put", reps=1, seed=5)
+    assert r2["cached"] and r2["fields_per_word"] == r["fields_per_word"]
