@@ -884,12 +884,14 @@ def run_kv(args, dev):
     return out
 
 
-def run_served(args, dev):
+def run_served(args, dev, rates=(0.25, 0.5, 0.9, 1.2, 1.5, 2.0)):
     """16 resident compact iceberg tables (48-bit keys, 2^20..2^23 primary
     buckets), Poisson request arrivals at rates relative to the saturated
     throughput, sizes log-uniform 256..4M keys, 60 % lookups / 30 %
     find-or-put / 10 % insert, 40 % re-queries: served with continuous
-    batching vs one synchronous launch per request."""
+    batching vs one synchronous launch per request. Requests carry key
+    recipes; their keys are generated on the device when they are admitted,
+    into a key arena whose size bounds what is in flight."""
     from paper_2406_09255_gb300 import ICEBERG, Table
     from paper_2406_09255_gb300 import workloads as W
     from paper_2406_09255_gb300.serve import (Server, latency_stats, make_requests,
@@ -924,7 +926,7 @@ def run_served(args, dev):
     srv.plan(reqs, seed=1)
     run_sequential(srv, reqs, realtime=False)
     results["saturated_sync"] = latency_stats(reqs)
-    for frac in (0.25, 0.5, 0.9, 1.2, 1.5, 2.0):
+    for frac in rates:
         rate = frac * sat_rate
         row = {}
         for mode in ("served", "sync_per_request"):
@@ -948,7 +950,8 @@ def run_served(args, dev):
            "config": {"workload": f"served: 16 compact iceberg tables (2^20..2^23 primary), "
                                   f"{n_req} requests, log-uniform 256..4M keys, 60/30/10 find/"
                                   f"fop/insert, 40% re-queries, Poisson arrivals"},
-           "saturated_request_rate": sat_rate, "results": results}
+           "saturated_request_rate": sat_rate, "arena_keys": srv.arena.cap,
+           "results": results}
     return out
 
 
@@ -1072,7 +1075,7 @@ def extra_configs(args, dev, compact_phases):
     section("iceberg_stream", lambda: run_iceberg_stream(_ap.Namespace(steps=3, warmup=1), dev))
     section("batch256", lambda: run_batch256(_ap.Namespace(steps=5, warmup=2), dev))
     section("bucket_sizes", lambda: run_bucket_sizes(_ap.Namespace(steps=2, warmup=1), dev))
-    section("served", lambda: run_served(few, dev))
+    section("served", lambda: run_served(few, dev, rates=(0.5, 0.9, 1.2)))
     return res
 
 
@@ -1091,7 +1094,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other configurations (whole-key tables, iceberg stream, "
                          "256-table batch, served loop) that follow the headline")
-    ap.add_argument("--requests", type=int, default=4000, help="served workload: request count")
+    ap.add_argument("--requests", type=int, default=100000,
+                    help="served workload: request count")
     ap.add_argument("--profile", choices=["find", "insert", "fop"],
                     help="run a small case for an ncu capture and exit")
     args = ap.parse_args()

@@ -19,6 +19,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcht.so")
+# the served benchmark's request-key generator: input generation, kept out of
+# the library
+GEN_SRC = os.path.join(PKG, "gen", "keygen.cu")
+GEN_LIB = os.path.join(PKG, "libchtgen.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -71,7 +75,22 @@ def build(verbose: bool = False, extra: list[str] | None = None, jobs: int | Non
             fcntl.flock(lk, fcntl.LOCK_UN)
 
 
+def _build_gen(verbose: bool) -> None:
+    if os.path.exists(GEN_LIB) and os.path.getmtime(GEN_LIB) >= os.path.getmtime(GEN_SRC):
+        return
+    tmp = GEN_LIB + f".{os.getpid()}.tmp"
+    cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", tmp,
+           GEN_SRC, "-lcudart"]
+    if verbose:
+        print(" ".join(cmd), flush=True)
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on keygen.cu:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, GEN_LIB)
+
+
 def _build_locked(verbose, extra, jobs) -> str:
+    _build_gen(verbose)
     extra = list(extra or [])
     srcs = sources()
     jobs = jobs or min(len(srcs), max(2, os.cpu_count() or 2))

@@ -1,13 +1,27 @@
 """Served request loop over resident tables: continuous batching.
 
 Requests (lookup, find-or-put or insert batches against one of several
-resident iceberg tables) arrive over time. The server admits every request
-that has arrived when it forms the next *wave*, as far as the free device
-memory budget and each table's headroom allow, and runs each wave as at most
-two fused multi-table launches (one lookup batch, one find-or-put batch). A
-wave is issued while the previous one is still on the GPU, on the other of
-two streams, so their work overlaps unless they touch a common table with a
-write, in which case the later wave waits for the earlier one's event.
+resident iceberg tables) arrive over time. The server admits the requests
+that have arrived when it forms the next *wave*, and runs each wave as at
+most two fused multi-table launches (one lookup batch, one find-or-put
+batch). A wave is issued while the previous one is still on the GPU, on the
+other of two streams, so their work overlaps unless they touch a common table
+with a write, in which case the later wave waits for the earlier one's event.
+
+Admission is by device memory and by table headroom:
+  - a request's keys and statuses live in a fixed key arena (device memory
+    sized from the free HBM when the server starts); a request is admitted
+    only when its keys fit in the arena next to the in-flight requests, and
+    its space returns when its wave completes. Requests are admitted in
+    arrival order: one that has to wait for memory holds back the ones behind
+    it, so a large request is not starved by small ones; a request larger
+    than the whole arena is rejected;
+  - a write request reserves its fresh keys against its table's headroom (a
+    share of the table's slots, max_fill) when it is admitted; one whose fresh
+    keys exceed the headroom left is rejected (a table never frees slots).
+Admitted requests get their keys generated on the device into their arena
+space (one generator launch per wave, from each request's key recipe), so the
+device holds only the keys of admitted requests.
 
 Per-table semantics equal running the requests one at a time in admission
 order: in one wave a table receives either a run of consecutive lookups
@@ -17,15 +31,15 @@ and in the mix; the only freedom is which of several copies of one new key
 inside one find-or-put request reports PUT (the others report FOUND), as for
 any concurrent find-or-put.
 
-Keys are planned in arrival order and generated on the device before serving
-starts (Server.plan), from each table's counter-based key sequence
-(workloads.keys_at): fresh keys take the table's next indices (capped by its
-headroom, so a table admits writes only while it has room), re-queries draw
-uniformly among the indices the table has been given before the request. The
-served inputs are thus resident in HBM when a request arrives.
+Key recipes (Server.plan, host only, O(1) per request): fresh keys take the
+table's next indices of its key sequence (capped at fill_cap of its slots,
+after which fresh draws become re-queries), lookups' fresh keys are
+never-inserted ones, re-queries draw uniformly among the indices the table
+has been given before the request (workloads.request_keys defines the keys).
 """
 from __future__ import annotations
 
+import collections
 import dataclasses
 import time
 
@@ -37,6 +51,7 @@ from .batch import OP_FIND, OP_FIND_OR_PUT, Batch
 from .table import Table
 
 FIND, FOP, INSERT = "find", "find_or_put", "insert"
+OK, WAIT, REJECT = "ok", "wait", "reject"
 
 
 @dataclasses.dataclass
@@ -47,30 +62,51 @@ class Request:
     n: int
     arrival: float          # seconds from the start of the run
     requery_frac: float = 0.4
-    # filled in by the server
+    # key recipe (Server.plan)
     n_fresh: int = 0
-    fresh_start: int = 0
+    fresh_base: int = 0
+    re_hi: int = 0
+    re_seed: int = 0
+    miss_base: int = 0
+    # filled in by the server
     admitted: float = -1.0
     done: float = -1.0
-    keys: torch.Tensor | None = None
-    status: torch.Tensor | None = None
+    rejected: str = ""
+    off: int = -1           # position of the request's keys in the key arena
+    keys: torch.Tensor | None = None    # kept with keep_results
+    status: torch.Tensor | None = None  # kept with keep_results
+
+    def recipe(self, key_bits: int, seed: int) -> dict:
+        return dict(n=self.n, n_fresh=self.n_fresh, fresh_base=self.fresh_base,
+                    re_hi=self.re_hi, re_seed=self.re_seed, miss_base=self.miss_base,
+                    key_bits=key_bits, seed=seed)
 
 
-def form_wave(pending: list, budget: int) -> tuple[list, list]:
-    """Split the pending requests (in admission order) into the next wave and
+def form_wave(pending: list, budget: int, admit=None) -> tuple[list, list]:
+    """Split the pending requests (in arrival order) into the next wave and
     the rest. Per table the wave takes a run of consecutive lookups or one
     write request, and no request is taken past an earlier one of its table
     that stays behind, so every table sees its requests in admission order.
     The wave holds at most budget keys, but always at least one request.
-    Linear in the number of pending requests."""
+
+    admit(r), if given, is asked for each request the wave could take: OK
+    takes it (its resources are then reserved), REJECT drops it (it is in
+    neither list; the caller has marked it), WAIT leaves it and every later
+    request for a later wave. Linear in the number of pending requests."""
     wave, rest, used, taken = [], [], 0, {}
     blocked = set()  # tables with an earlier request left for a later wave
-    for r in pending:
+    for i, r in enumerate(pending):
         kind = "r" if r.op == FIND else "w"
         cur = taken.get(r.table)
         fits = used + r.n <= budget or not wave
         ok = fits and (cur is None or (cur == "r" and kind == "r"))
         if ok and r.table not in blocked:
+            verdict = admit(r) if admit is not None else OK
+            if verdict == REJECT:
+                continue
+            if verdict == WAIT:
+                rest.extend(pending[i:])
+                return wave, rest
             wave.append(r)
             used += r.n
             taken[r.table] = kind
@@ -80,13 +116,68 @@ def form_wave(pending: list, budget: int) -> tuple[list, list]:
     return wave, rest
 
 
+class KeyArena:
+    """A ring of `cap` key positions handed out in admission order and given
+    back in any order; space is reused once every earlier allocation has been
+    given back. Host bookkeeping only."""
+
+    def __init__(self, cap: int):
+        self.cap = cap
+        self.live = collections.deque()  # [start, end, freed] in allocation order
+        self.tail = 0                    # where the next allocation may start
+
+    def used(self) -> int:
+        return sum(e - s for s, e, _ in self.live)
+
+    def alloc(self, n: int):
+        """Start of n free consecutive positions, or None (-1 for n = 0:
+        nothing to hold)."""
+        if n > self.cap:
+            return None
+        if n == 0:
+            return -1
+        if not self.live:
+            self.tail = start = 0
+        else:
+            head = self.live[0][0]
+            if self.tail > head:
+                # in use: [head, tail); free: [tail, cap), then [0, head)
+                if self.tail + n <= self.cap:
+                    start = self.tail
+                elif n <= head:
+                    start = 0
+                else:
+                    return None
+            else:
+                # wrapped: in use [head, cap) and [0, tail); free: [tail, head)
+                if self.tail + n <= head:
+                    start = self.tail
+                else:
+                    return None
+        self.live.append([start, start + n, False])
+        self.tail = start + n
+        return start
+
+    def free(self, start: int) -> None:
+        if start < 0:
+            return
+        for item in self.live:
+            if item[0] == start and not item[2]:
+                item[2] = True
+                break
+        while self.live and self.live[0][2]:
+            self.live.popleft()
+
+
 @dataclasses.dataclass
 class TableState:
     table: Table
     seed: int
     key_bits: int
-    capacity: int            # keys the table may receive before it counts as full
-    next_index: int = 0      # next fresh key index of this table's sequence
+    capacity: int            # fresh keys the workload gives the table (fill_cap)
+    limit: int               # keys the server lets requests reserve (max_fill)
+    next_index: int = 0      # next fresh key index of this table's sequence (plan)
+    reserved: int = 0        # fresh keys reserved by admitted write requests
     absent_base: int = 1 << 40
 
 
@@ -94,85 +185,85 @@ class Server:
     """Continuous-batching request loop over resident iceberg tables."""
 
     def __init__(self, tables: list[Table], seeds: list[int], *, fill_cap: float = 0.85,
-                 max_wave_keys: int = 1 << 25, hbm_reserve: float = 0.1, device=None):
+                 max_fill: float = 0.95, arena_keys: int | None = None,
+                 hbm_fraction: float = 0.25, max_wave_keys: int = 1 << 25,
+                 keep_results: bool = False, device=None):
         self.dev = device or tables[0].device
         self.states = []
         for t, s in zip(tables, seeds):
-            cap = int(fill_cap * t.slots)
-            self.states.append(TableState(t, s, t.cfg.key_bits, cap,
+            self.states.append(TableState(t, s, t.cfg.key_bits, int(fill_cap * t.slots),
+                                          int(max_fill * t.slots),
                                           absent_base=1 << (t.cfg.key_bits - 2)))
+        if arena_keys is None:
+            free, _ = torch.cuda.mem_get_info(self.dev)
+            arena_keys = int(min(1 << 28, hbm_fraction * free / 9))  # 8 B key + 1 B status
+        self.arena = KeyArena(arena_keys)
+        self.keys = torch.empty(arena_keys, dtype=torch.int64, device=self.dev)
+        self.status = torch.empty(arena_keys, dtype=torch.uint8, device=self.dev)
         self.max_wave_keys = max_wave_keys
-        self.hbm_reserve = hbm_reserve
+        self.keep_results = keep_results
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(2)]
         self.waves = 0
         self.launches = 0
-        self._budget = None  # (keys, time taken)
+        self.rejected = 0
+        self.held_for_memory = set()  # requests that had to wait for arena space
 
-    # -- admission ------------------------------------------------------------
-    def _budget_keys(self, refresh_s: float = 0.01) -> int:
-        """Keys a wave may admit given free HBM (re-read at most every
-        refresh_s: the query is a driver call that costs the served loop)."""
-        now = time.perf_counter()
-        if self._budget is None or now - self._budget[1] > refresh_s:
-            free, total = torch.cuda.mem_get_info(self.dev)
-            usable = max(0, free - self.hbm_reserve * total)
-            # per admitted key: its status byte plus staging of fused launches
-            self._budget = (int(min(self.max_wave_keys, usable // 16)), now)
-        return self._budget[0]
-
+    # -- key recipes ---------------------------------------------------------
     def plan(self, requests: list[Request], seed: int = 0) -> list[Request]:
-        """Give every request its keys, in arrival order: fresh keys take the
-        table's next indices (capped by its headroom), lookups' fresh keys are
-        never-inserted ones, re-queries draw uniformly among the indices the
-        table has been given before the request. Keys are generated on the
-        device, one vectorised pass per table, and stay resident."""
+        """Give every request its key recipe, in arrival order: fresh keys
+        take the table's next indices (capped at fill_cap of its slots),
+        lookups' fresh keys are never-inserted ones, re-queries draw uniformly
+        among the indices the table has been given before the request. Host
+        arithmetic only: keys are generated when a request is admitted."""
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
-        per_table: dict[int, list] = {}
         for r in reqs:
             st = self.states[r.table]
             want = int(round((1 - r.requery_frac) * r.n))
+            r.re_hi = st.next_index
+            r.re_seed = W.splitmix(seed, r.rid)
+            r.miss_base = st.absent_base + r.rid * (1 << 23) + (1 << 22)
             if r.op == FIND:
-                r.n_fresh, r.fresh_start = want, -1
-                hi = st.next_index
+                r.n_fresh = want
+                r.fresh_base = st.absent_base + r.rid * (1 << 23)
             else:
                 r.n_fresh = min(want, max(0, st.capacity - st.next_index))
-                r.fresh_start = st.next_index
-                hi = st.next_index
+                r.fresh_base = st.next_index
                 st.next_index += r.n_fresh
-            per_table.setdefault(r.table, []).append((r, hi))
-        g = torch.Generator(device=self.dev)
-        g.manual_seed(seed)
-        for tid, items in per_table.items():
-            st = self.states[tid]
-            idx_parts = []
-            for r, hi in items:
-                n_re = r.n - r.n_fresh
-                if r.op == FIND:
-                    base = st.absent_base + r.rid * (1 << 23)
-                    fresh = torch.arange(base, base + r.n_fresh, device=self.dev)
-                else:
-                    fresh = torch.arange(r.fresh_start, r.fresh_start + r.n_fresh,
-                                         device=self.dev)
-                if hi > 0:
-                    u = torch.rand(n_re, generator=g, device=self.dev, dtype=torch.float64)
-                    re = (u * hi).to(torch.int64).clamp_(max=hi - 1)
-                else:  # nothing given yet: re-queries become misses
-                    base = st.absent_base + r.rid * (1 << 23) + (1 << 22)
-                    re = torch.arange(base, base + n_re, device=self.dev)
-                idx_parts.append(torch.cat([fresh, re]))
-            allk = W.keys_at(torch.cat(idx_parts), st.key_bits, st.seed)
-            off = 0
-            for r, _ in items:
-                r.keys = allk[off: off + r.n]
-                off += r.n
         return reqs
 
-    # -- running --------------------------------------------------------------
+    def request_keys(self, r: Request, device="cpu") -> torch.Tensor:
+        """Request r's keys computed with torch (the generator's definition)."""
+        st = self.states[r.table]
+        return W.request_keys(r.n, r.n_fresh, r.fresh_base, r.re_hi, r.re_seed, r.miss_base,
+                              st.key_bits, st.seed, device)
+
+    # -- admission -------------------------------------------------------------
+    def _admit(self, r: Request, now: float) -> str:
+        st = self.states[r.table]
+        if r.op != FIND and r.n_fresh > st.limit - st.reserved:
+            r.rejected = "table headroom"
+        elif r.n > self.arena.cap:
+            r.rejected = "larger than the key arena"
+        if r.rejected:
+            r.admitted = r.done = now
+            self.rejected += 1
+            return REJECT
+        off = self.arena.alloc(r.n)
+        if off is None:
+            self.held_for_memory.add(r.rid)
+            return WAIT
+        r.off = off
+        if r.op != FIND:
+            st.reserved += r.n_fresh
+        return OK
+
+    # -- running -------------------------------------------------------------
     def run(self, requests: list[Request], *, realtime: bool = True):
         """Serve planned requests (see plan). With realtime, a request is
         visible only once the wall clock passes its arrival time. Returns the
-        requests with admitted/done times and status tensors filled in."""
-        reqs = sorted(requests, key=lambda r: r.arrival)
+        requests with admitted/done times (and, with keep_results, their keys
+        and statuses) filled in."""
+        reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
         pending: list[Request] = []
         inflight = []   # (event, requests, write_tables, all_tables)
         nxt = 0
@@ -190,6 +281,7 @@ class Server:
                     tdone = time.perf_counter() - t0
                     for r in rs:
                         r.done = tdone
+                        self.arena.free(r.off)
                 else:
                     still.append((ev, rs, wt, at))
             inflight = still
@@ -201,14 +293,36 @@ class Server:
                     if gap > 2e-4:
                         time.sleep(min(0.001, gap - 2e-4))
                 continue
-            wave, pending = form_wave(pending, self._budget_keys())
             tnow = time.perf_counter() - t0
+            wave, pending = form_wave(pending, self.max_wave_keys,
+                                      lambda r: self._admit(r, tnow))
+            if not wave:
+                continue  # held for memory (or all rejected): wait for a wave to finish
             for r in wave:
                 r.admitted = tnow
             self._issue(wave, slot, inflight)
             slot ^= 1
         torch.cuda.synchronize()
         return reqs
+
+    def _generate(self, wave: list, stream) -> None:
+        """The wave's keys into the arena: one generator launch per 128
+        requests (positions in arena order)."""
+        recs = []
+        for r in sorted(wave, key=lambda r: r.off):
+            if r.n:
+                st = self.states[r.table]
+                recs.append(dict(r.recipe(st.key_bits, st.seed), out_off=r.off))
+        # a launch covers a contiguous span of the arena; requests that
+        # wrapped around its end go into a launch of their own
+        span = []
+        for d in recs:
+            if span and d["out_off"] < span[-1]["out_off"] + span[-1]["n"]:
+                W.request_keys_device(span, self.keys, stream)
+                span = []
+            span.append(d)
+        if span:
+            W.request_keys_device(span, self.keys, stream)
 
     def _issue(self, wave, slot, inflight):
         s = self.streams[slot]
@@ -219,8 +333,9 @@ class Server:
             if (writes & at) or (wt & touched):
                 s.wait_event(ev)
         with torch.cuda.stream(s):
-            for r in wave:
-                r.status = torch.empty(r.n, dtype=torch.uint8, device=self.dev)
+            self._generate(wave, s)
+            view = {r.rid: (self.keys[r.off: r.off + r.n], self.status[r.off: r.off + r.n])
+                    for r in wave}
             finds = [r for r in wave if r.op == FIND and r.n]
             fops = [r for r in wave if r.op != FIND and r.n]
             for group, op in ((finds, OP_FIND), (fops, OP_FIND_OR_PUT)):
@@ -230,14 +345,16 @@ class Server:
                     # a lone request needs no fused plan: one direct launch
                     r = group[0]
                     t = self.states[r.table].table
+                    k, st = view[r.rid]
                     if op == OP_FIND:
-                        t.find(r.keys, status=r.status, stream=s)
+                        t.find(k, status=st, stream=s)
                     else:
-                        t.find_or_put(r.keys, status=r.status, stream=s)
+                        t.find_or_put(k, status=st, stream=s)
                     self.launches += 1
                     continue
-                # one fused launch; several lookups of one table are
-                # concatenated into one entry (lookups commute)
+                # one fused launch; several lookups of one table become one
+                # entry over their keys (lookups commute); their arena ranges
+                # are gathered into one key array
                 by_table: dict[int, list[Request]] = {}
                 for r in group:
                     by_table.setdefault(r.table, []).append(r)
@@ -245,10 +362,11 @@ class Server:
                 for tid, rs in by_table.items():
                     tabs.append(self.states[tid].table)
                     if len(rs) == 1:
-                        keys.append(rs[0].keys)
-                        sts.append(rs[0].status)
+                        k, st = view[rs[0].rid]
+                        keys.append(k)
+                        sts.append(st)
                     else:
-                        keys.append(torch.cat([r.keys for r in rs]))
+                        keys.append(torch.cat([view[r.rid][0] for r in rs]))
                         sts.append(torch.empty(sum(r.n for r in rs), dtype=torch.uint8,
                                                device=self.dev))
                         splits.append((sts[-1], rs))
@@ -258,8 +376,12 @@ class Server:
                 for big, rs in splits:
                     off = 0
                     for r in rs:
-                        r.status.copy_(big[off: off + r.n])
+                        view[r.rid][1].copy_(big[off: off + r.n])
                         off += r.n
+            if self.keep_results:
+                for r in wave:
+                    k, st = view[r.rid]
+                    r.keys, r.status = k.clone(), st.clone()
             ev = torch.cuda.Event()
             ev.record(s)
         self.waves += 1
@@ -268,21 +390,34 @@ class Server:
 
 def run_sequential(server: Server, requests: list[Request], *, realtime: bool = True):
     """Baseline: one synchronous launch per request, in arrival order (the
-    requests must have been planned by `server`)."""
+    requests must have been planned by `server`; same admission rules, the
+    arena holding one request at a time)."""
     reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
     t0 = time.perf_counter()
+    s = torch.cuda.current_stream(server.dev)
     for r in reqs:
         if realtime:
             while time.perf_counter() - t0 < r.arrival:
                 pass
         r.admitted = time.perf_counter() - t0
-        t = server.states[r.table].table
+        if server._admit(r, r.admitted) == REJECT:
+            continue
         if r.n:
-            r.status = t.find(r.keys) if r.op == FIND else t.find_or_put(r.keys)
-        else:
+            server._generate([r], s)
+            k, st = server.keys[r.off: r.off + r.n], server.status[r.off: r.off + r.n]
+            t = server.states[r.table].table
+            if r.op == FIND:
+                t.find(k, status=st)
+            else:
+                t.find_or_put(k, status=st)
+            if server.keep_results:
+                r.keys, r.status = k.clone(), st.clone()
+        elif server.keep_results:
+            r.keys = torch.empty(0, dtype=torch.int64, device=server.dev)
             r.status = torch.empty(0, dtype=torch.uint8, device=server.dev)
         torch.cuda.synchronize()
         r.done = time.perf_counter() - t0
+        server.arena.free(r.off)
     return reqs
 
 
@@ -301,9 +436,10 @@ def make_requests(n: int, n_tables: int, rate_per_s: float, *, min_size: int = 2
 
 
 def latency_stats(reqs: list[Request]) -> dict:
-    lat = np.array([r.done - r.arrival for r in reqs if r.done >= 0])
-    keys = sum(r.n for r in reqs)
-    span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+    served = [r for r in reqs if r.done >= 0 and not r.rejected]
+    lat = np.array([r.done - r.arrival for r in served])
+    keys = sum(r.n for r in served)
+    span = max(r.done for r in served) - min(r.arrival for r in reqs)
     return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_ms": float(lat.mean() * 1e3), "mops": keys / span / 1e6, "requests": len(reqs),
-            "keys": keys, "span_s": span}
+            "mean_ms": float(lat.mean() * 1e3), "mops": keys / span / 1e6, "requests": len(served),
+            "rejected": len(reqs) - len(served), "keys": keys, "span_s": span}

@@ -17,7 +17,9 @@ and on the GPU and gives identical values.
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
 
 import numpy as np
 import torch
@@ -332,3 +334,110 @@ def multi_table_spec(count: int = 256, lo_exp: int = 8, hi_exp: int = 18,
         s = int(min(s, cap))
         out.append((int(e), s, int(distinct_frac * s)))
     return out
+
+
+# --- request keys of the served benchmark -----------------------------------
+# A request's keys are n_fresh keys at consecutive indices from fresh_base,
+# then n - n_fresh re-queries: index floor(h * re_hi / 2^64) with h the j-th
+# output of the splitmix64 sequence of re_seed (j = 0, 1, ...), or, when
+# re_hi is 0 (a table with nothing given yet), consecutive indices from
+# miss_base. Keys are G_s at those indices (keys_at). The same definition is
+# computed here with torch (request_keys) and on the device by the generator
+# kernel of gen/keygen.cu (request_keys_device), so that a served run holds
+# only the keys of admitted requests.
+
+def _mulhi_small(h: torch.Tensor, m: int) -> torch.Tensor:
+    """floor(h * m / 2^64) for int64 tensors h holding 64-bit unsigned bits
+    and 0 <= m < 2^31."""
+    assert 0 <= m < (1 << 31)
+    h0 = h & 0xFFFFFFFF
+    h1 = _srl(h, 32)
+    t = h1 * m + _srl(h0 * m, 32)
+    return _srl(t, 32)
+
+
+def request_indices(n: int, n_fresh: int, fresh_base: int, re_hi: int, re_seed: int,
+                    miss_base: int, device="cpu") -> torch.Tensor:
+    """The key indices of one request (see above)."""
+    fresh = torch.arange(fresh_base, fresh_base + n_fresh, dtype=torch.int64, device=device)
+    n_re = n - n_fresh
+    if n_re <= 0:
+        return fresh
+    j = torch.arange(n_re, dtype=torch.int64, device=device)
+    if re_hi:
+        h = mix64_t(_s64(re_seed) + (j + 1) * _s64(GAMMA))
+        re = _mulhi_small(h, re_hi)
+    else:
+        re = miss_base + j
+    return torch.cat([fresh, re])
+
+
+def request_keys(n: int, n_fresh: int, fresh_base: int, re_hi: int, re_seed: int,
+                 miss_base: int, key_bits: int, seed: int, device="cpu") -> torch.Tensor:
+    """The keys of one request, computed with torch (int64)."""
+    return keys_at(request_indices(n, n_fresh, fresh_base, re_hi, re_seed, miss_base, device),
+                   key_bits, seed)
+
+
+class _GenReq(ctypes.Structure):
+    """One request descriptor of the device generator (gen/keygen.cu)."""
+    _fields_ = [("out_off", ctypes.c_uint64), ("n", ctypes.c_uint64),
+                ("n_fresh", ctypes.c_uint64), ("fresh_base", ctypes.c_uint64),
+                ("re_hi", ctypes.c_uint64), ("re_seed", ctypes.c_uint64),
+                ("miss_base", ctypes.c_uint64), ("rk", ctypes.c_uint64 * 4),
+                ("skip", ctypes.c_uint64), ("key_bits", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+_gen_lib = None
+
+
+def _gen():
+    global _gen_lib
+    if _gen_lib is None:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libchtgen.so")
+        if not os.path.exists(path):
+            raise RuntimeError("libchtgen.so is missing: build the package first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(path)
+        L.keygen_request_keys.restype = ctypes.c_int
+        L.keygen_request_keys.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                          ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        assert L.keygen_req_bytes() == ctypes.sizeof(_GenReq)
+        _gen_lib = L
+    return _gen_lib
+
+
+def request_keys_device(reqs: list, out: torch.Tensor, stream=None) -> None:
+    """Write the keys of several requests into the int64 device tensor out.
+
+    reqs: dicts with out_off (position in out, ascending), n, n_fresh,
+    fresh_base, re_hi, re_seed, miss_base, key_bits, seed. One kernel launch
+    per 128 requests, on stream (default: the current stream)."""
+    import ctypes
+    L = _gen()
+    per = L.keygen_req_per_launch()
+    s = stream if stream is not None else torch.cuda.current_stream(out.device)
+    sms = torch.cuda.get_device_properties(out.device).multi_processor_count
+    for i0 in range(0, len(reqs), per):
+        part = reqs[i0: i0 + per]
+        arr = (_GenReq * len(part))()
+        for d, r in zip(arr, part):
+            d.out_off, d.n, d.n_fresh = r["out_off"], r["n"], r["n_fresh"]
+            d.fresh_base, d.re_hi = r["fresh_base"], r["re_hi"]
+            d.re_seed, d.miss_base = _u64(r["re_seed"]), r["miss_base"]
+            for k, v in enumerate(_round_keys(r["seed"])):
+                d.rk[k] = v
+            d.skip = key_index_skip(r["key_bits"], r["seed"])
+            d.key_bits = r["key_bits"]
+        base = part[0]["out_off"]
+        total = part[-1]["out_off"] + part[-1]["n"] - base
+        # positions are relative to the first request of this launch
+        for d in arr:
+            d.out_off -= base
+        if total == 0:
+            continue
+        code = L.keygen_request_keys(ctypes.addressof(arr), len(part), total,
+                                     out.data_ptr() + 8 * base, sms,
+                                     ctypes.c_void_p(s.cuda_stream))
+        if code:
+            raise RuntimeError(f"request key generator launch failed (CUDA error {code})")

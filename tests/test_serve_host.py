@@ -3,6 +3,8 @@ consecutive lookups or one write, admission order kept per table, the key
 budget respected, and every request eventually served."""
 import random
 
+import torch
+
 from paper_2406_09255_gb300.serve import FIND, FOP, INSERT, Request, form_wave
 
 
@@ -53,3 +55,66 @@ def test_random_streams_keep_per_table_order_and_drain():
     for t in range(4):
         ids = [r.rid for r in served if r.table == t]
         assert ids == sorted(ids), "a table sees its requests in admission order"
+
+
+def test_admission_wait_keeps_arrival_order_and_reject_drops():
+    from paper_2406_09255_gb300.serve import OK, REJECT, WAIT
+    p = reqs([(0, FIND, 10), (1, FOP, 500), (2, FIND, 10), (3, FOP, 7)])
+    verdicts = {0: OK, 1: WAIT, 2: OK, 3: OK}
+    wave, rest = form_wave(p, 10 ** 9, lambda r: verdicts[r.rid])
+    # the request that waits for memory holds back everything behind it
+    assert [r.rid for r in wave] == [0] and [r.rid for r in rest] == [1, 2, 3]
+    verdicts = {0: OK, 1: REJECT, 2: OK, 3: OK}
+    wave, rest = form_wave(p, 10 ** 9, lambda r: verdicts[r.rid])
+    assert [r.rid for r in wave] == [0, 2, 3] and rest == []
+
+
+def test_key_arena_never_overlaps_and_reuses_space():
+    from paper_2406_09255_gb300.serve import KeyArena
+    rnd = random.Random(1)
+    a = KeyArena(100)
+    live = {}
+    for _ in range(20000):
+        if live and rnd.random() < 0.5:
+            s = rnd.choice(list(live))
+            a.free(s)
+            del live[s]
+        else:
+            n = rnd.randrange(0, 60)
+            s = a.alloc(n)
+            if s is None or n == 0:
+                continue
+            assert 0 <= s and s + n <= 100
+            for t, m in live.items():
+                assert s + n <= t or t + m <= s
+            live[s] = n
+    for s in list(live):
+        a.free(s)
+    assert a.used() == 0 and a.alloc(100) == 0
+    assert a.alloc(1) is None      # full
+    assert a.alloc(101) is None    # larger than the arena
+
+
+def test_key_arena_waits_for_the_oldest_allocation():
+    from paper_2406_09255_gb300.serve import KeyArena
+    a = KeyArena(10)
+    x, y = a.alloc(6), a.alloc(4)
+    assert (x, y) == (0, 6)
+    a.free(y)                # freed out of order: space comes back only once
+    assert a.alloc(4) is None  # the older allocation x is given back too
+    a.free(x)
+    assert a.alloc(10) == 0
+
+
+def test_request_keys_definition():
+    """Fresh keys at consecutive indices, re-queries at floor(h * hi / 2^64)
+    with h = splitmix64(re_seed, j), misses at consecutive indices when
+    nothing was given yet; keys are the key sequence at those indices."""
+    from paper_2406_09255_gb300 import workloads as W
+    idx = W.request_indices(10, 3, 100, 12345, 777, 1 << 40)
+    want = list(range(100, 103)) + [(W.splitmix(777, j) * 12345) >> 64 for j in range(7)]
+    assert idx.tolist() == want
+    idx = W.request_indices(5, 2, 7, 0, 3, 1000)
+    assert idx.tolist() == [7, 8, 1000, 1001, 1002]
+    k = W.request_keys(10, 3, 100, 12345, 777, 1 << 40, 48, 99)
+    assert k.tolist() == W.keys_at(torch.tensor(want), 48, 99).tolist()
