@@ -86,7 +86,7 @@ def test_concurrent_cuckoo_lookups_small_buckets(wpb):
     assert (st == P.PUT).all()
     stored, cnt = t.enumerate()
     assert np.array_equal(np.sort(u64(stored)), np.sort(keys.numpy().astype(np.uint64)))
-    q, present = W.find_queries(n, 1 << 18, 0.5, w, 77, n)
+    q, present = W.find_queries(n, 1 << 17, 0.5, w, 77, n)
     ctr = t.attach_counters()
     got = t.find(W.to_u32(q).to(DEV)).cpu().numpy()
     torch.cuda.synchronize()
@@ -102,9 +102,11 @@ def test_concurrent_cuckoo_lookups_small_buckets(wpb):
 
 @pytest.mark.parametrize("wpb", [4, 8])
 def test_concurrent_iceberg_small_buckets(wpb):
+    # 8- and 16-slot primary buckets overflow earlier than 32-slot ones
+    # (Section 5.2): a stash takes the keys whose three buckets fill up
     P = cht()
     w = 40
-    t = P.Table(P.ICEBERG, w, 1 << 10, 1 << 7, bucket_words=wpb, seed=12)
+    t = P.Table(P.ICEBERG, w, 1 << 10, 1 << 7, bucket_words=wpb, stash_slots=4096, seed=12)
     fresh = W.unique_keys(0, int(0.7 * t.slots), w, 5)
     rng = np.random.default_rng(2)
     keys = torch.cat([fresh, fresh[torch.from_numpy(rng.integers(0, len(fresh), len(fresh)))]])
@@ -121,7 +123,7 @@ def test_concurrent_iceberg_small_buckets(wpb):
     assert np.array_equal(np.sort(u64(stored)), np.sort(o.enumerate()))
     d = dump_into(mirror(t), t)
     assert d.check_entries() == 0 and d.check_order_property() == 0 and d.check_prefix() == 0
-    assert d.check_duplicates() == 0
+    assert d.check_duplicates() == 0 and d.check_stash() == 0
     q = W.unique_keys(0, len(fresh) + 5000, w, 5)
     got = t.find(q.to(DEV)).cpu().numpy()
     assert (got == d.find(q.numpy().astype(np.uint64))).all()
