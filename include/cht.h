@@ -102,17 +102,21 @@ typedef struct cht_table cht_table; /* opaque host handle */
  * max_tiles             upper bound on tiles that take work (0 = no bound).
  *                       With max_tiles = 1 a single tile processes the keys
  *                       strictly in input order (a sequential run).
- * lookups_in_flight     bucket loads a tile keeps in flight in cht_find and
- *                       cht_insert on cuckoo tables: 1, 4 or 8 (0 = 4). With
- *                       1 each tile walks its pending keys one load at a
- *                       time (puts: chunks of items_per_thread keys per
- *                       lane); with 4 or 8 every lane holds a key, each
- *                       round takes one step of all of a tile's keys with
- *                       that many loads issued back to back (puts also issue
- *                       that many claims before reading any), and answered
- *                       lanes take the next key (a stream of fully packed
- *                       rounds). Lookup answers and probe counts are the
- *                       same for every value. Iceberg operations ignore it.
+ * lookups_in_flight     bucket loads a tile keeps in flight: 1, 4 or 8 (0 =
+ *                       4 for cuckoo tables, 1 for iceberg tables). With 1
+ *                       each tile walks its pending keys one load at a time
+ *                       (chunks of items_per_thread keys per lane); with 4
+ *                       or 8 every lane holds a key, each round takes one
+ *                       step of all of a tile's keys with that many loads
+ *                       issued back to back (puts and find-or-puts also
+ *                       issue that many claims before reading any), and
+ *                       answered lanes take the next key (a stream of fully
+ *                       packed rounds). For iceberg find-or-put and lookups
+ *                       the stream covers the primary level, and a second
+ *                       pass takes the keys whose primary bucket was full
+ *                       through level 2 (and the stash). Answers (lookups;
+ *                       one PUT per absent key) are the same for every
+ *                       value; runs with slot outputs or value moves use 1.
  * retry_limit           iceberg find-or-put: lost claims a key may retry
  *                       before it gives up with status CHT_ERROR, 0..32767
  *                       (0 = the built-in bound, which a correct run never

@@ -152,7 +152,8 @@ int resolve(const cht_config *in, cht_config *out) {
             !is_pow2((uint64_t)c.stash_slots))
             return fail(CHT_ERR_INVALID, "stash_slots must be 0 or a power of two in [2, 2^30]");
     }
-    if (c.lookups_in_flight == 0) c.lookups_in_flight = 4;
+    // cuckoo: the stream kernels; iceberg: the warp-batched chunk engine
+    if (c.lookups_in_flight == 0) c.lookups_in_flight = c.kind == CHT_ICEBERG ? 1 : 4;
     if (c.lookups_in_flight != 1 && c.lookups_in_flight != 4 && c.lookups_in_flight != 8)
         return fail(CHT_ERR_INVALID, "lookups_in_flight must be 1, 4 or 8");
     *out = c;

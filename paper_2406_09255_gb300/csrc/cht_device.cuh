@@ -32,6 +32,9 @@ constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 // status bytes (mirror include/cht.h)
 constexpr uint8_t ST_NOT_FOUND = 0, ST_FOUND = 1, ST_PUT = 2, ST_FULL = 3,
                   ST_INVALID = 4, ST_ERROR = 5;
+// internal, never left in a caller's status array: an iceberg key whose
+// level-1 step found its primary bucket full and that awaits level 2
+constexpr uint8_t ST_PENDING = 6;
 
 // One level of a table (cuckoo table, iceberg primary or iceberg secondary).
 struct Level {

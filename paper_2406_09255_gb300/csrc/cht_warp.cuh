@@ -78,8 +78,10 @@ struct BatchSource {
 // SLOTS: also write each FOUND / PUT key's slot index to the chunk's slots
 // array (the key-value extension); a separate instantiation, so that plain
 // runs pay nothing for it
+// RESUME: take only the keys whose status is ST_PENDING (left by the level-1
+// stream kernel), start them at level 2, and write only their statuses
 template <int T, int FPW0, int I, bool LOOKUP, class Src, bool SLOTS = false,
-          int WPB = kWordsPerBucket>
+          int WPB = kWordsPerBucket, bool RESUME = false>
 __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long *ctr) {
     constexpr int W = WPB / T;
     constexpr uint32_t TM = (T == 32) ? 0xffffffffu : ((1u << T) - 1u);
@@ -124,12 +126,14 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
             slot_of[i] = ~0ull;
             vpre[i] = KVal{0, 0};
             const int pos = i * 32 + lane;
-            const bool has = pos < ch.count;
+            bool has = pos < ch.count;
+            if constexpr (RESUME) has = has && ch.status[ch.base + pos] == ST_PENDING;
             k[i] = has ? load_key(ch.keys, ta.key_bytes, ch.base + pos) : 0;
             if (!LOOKUP && moves && has) vpre[i] = kv_read(ch.kv->vin, ch.base + pos, ch.kv->vbytes);
             pending[i] = has && valid_key(k[i], ta.w);
             st[i] = pending[i] ? ST_NOT_FOUND : ST_INVALID;
-            lvl2[i] = lvl3[i] = false;
+            lvl2[i] = RESUME;
+            lvl3[i] = false;
             it[i] = 0;
             const Quot q = quotient(L0, ta.w, 0, k[i]);
             a0[i] = (uint32_t)q.a;
@@ -449,7 +453,9 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
 #pragma unroll
         for (int i = 0; i < I; ++i) {
             const int pos = i * 32 + lane;
-            if (pos < ch.count) {
+            // a resumed run writes back only the keys it took (valid keys
+            // reach the end with a final status: pending is false)
+            if (pos < ch.count && (!RESUME || k[i] != 0)) {
                 ch.status[ch.base + pos] = st[i];
                 if constexpr (SLOTS) {
                     if (ch.slots) ch.slots[ch.base + pos] = slot_of[i];
@@ -461,7 +467,7 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
                     }
                 }
             }
-            n_ops += pos < ch.count ? 1 : 0;
+            n_ops += (!RESUME && pos < ch.count) ? 1 : 0;
         }
     }
     if (ctr) {
@@ -480,6 +486,16 @@ __global__ void __launch_bounds__(256, 5)
                    uint8_t *__restrict__ status) {
     SingleSource src{&ta, keys, status, nullptr, nullptr, n, (uint64_t)32 * I};
     iceberg_warp<T, FPW0, I, LOOKUP, SingleSource, false, WPB>(src, ta.ctr);
+}
+
+// level 2 (and the stash) for the keys the level-1 stream kernel left
+// pending; one key per lane, five blocks per SM as for the engine above
+template <int T, int FPW0, bool LOOKUP, int WPB = kWordsPerBucket>
+__global__ void __launch_bounds__(256, 5)
+    k_iceberg_resume(TableArgs ta, const void *__restrict__ keys, uint64_t n,
+                     uint8_t *__restrict__ status) {
+    SingleSource src{&ta, keys, status, nullptr, nullptr, n, 32};
+    iceberg_warp<T, FPW0, 1, LOOKUP, SingleSource, false, WPB, true>(src, ta.ctr);
 }
 
 // with slot outputs and value moves (one key per lane); held to 64 registers

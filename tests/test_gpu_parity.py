@@ -280,6 +280,57 @@ def test_iceberg_fop_duplicates_parity(T, items):
     assert t.error_flags() == 0
 
 
+@pytest.mark.parametrize("T,P", [(4, 4), (8, 4), (4, 8), (16, 8)])
+def test_iceberg_stream_form_parity(T, P):
+    """The stream form (level 1 in packed rounds with P loads in flight per
+    tile, then a level-2 pass over the keys whose primary was full) meets the
+    same contract as the chunk engine: one PUT per distinct key, the oracle's
+    stored set, a well-formed dump, exact lookups (also in the stream form),
+    and no key left pending."""
+    w = 40
+    t = cht().Table(cht().ICEBERG, w, 1 << 12, 1 << 9, seed=23, tile=T, lookups_in_flight=P)
+    o = mirror(t)
+    n_fresh = int(0.85 * t.slots)
+    keys = W.duplicate_stream(2 * n_fresh, n_fresh, w, 57, 0.5)
+    st = t.find_or_put(keys.to(DEV)).cpu().numpy()
+    kn = keys.numpy().astype(np.uint64)
+    ost = o.insert(kn)
+    assert (ost != oracle.FULL).all() and (st != 6).all()
+    _fop_contract(t, kn, st, o.enumerate())
+    q, present = W.find_queries(n_fresh, 60000, 0.5, w, 57, 2 * n_fresh)
+    got = t.find(q.to(DEV)).cpu().numpy()
+    assert np.array_equal(got == cht().FOUND, present.numpy())
+    d = dump_into(mirror(t), t)
+    assert (d.find(q.numpy().astype(np.uint64)) == got).all()
+    assert t.error_flags() == 0
+
+
+@pytest.mark.parametrize("P", [4, 8])
+def test_iceberg_stream_form_past_capacity_with_stash(P):
+    w = 36
+    t = cht().Table(cht().ICEBERG, w, 1 << 8, 1 << 5, seed=18, lookups_in_flight=P,
+                    stash_slots=256)
+    fresh = W.unique_keys(0, int(1.1 * t.slots), w, 4)
+    rng = np.random.default_rng(3)
+    keys = torch.cat([fresh, fresh[torch.from_numpy(rng.integers(0, len(fresh), len(fresh)))]])
+    keys = keys[torch.from_numpy(rng.permutation(len(keys)))]
+    kn = keys.numpy().astype(np.uint64)
+    st = t.find_or_put(keys.to(DEV)).cpu().numpy()
+    P_ = cht()
+    assert (st == P_.FULL).sum() > 0 and (st != 6).all()
+    d = dump_into(mirror(t), t)
+    assert (d.stash != 0).all()
+    assert d.check_entries() == 0 and d.check_order_property() == 0 and d.check_prefix() == 0
+    assert d.check_stash() == 0 and d.check_duplicates() == 0
+    stored = set(d.enumerate().tolist())
+    uniq, inv = np.unique(kn, return_inverse=True)
+    puts = np.bincount(inv, weights=(st == P_.PUT), minlength=len(uniq))
+    assert set(uniq[puts == 1].tolist()) == stored and puts.max() == 1
+    assert set(kn[st == P_.FULL].tolist()).isdisjoint(stored)
+    got = t.find(keys.to(DEV)).cpu().numpy()
+    assert (got == d.find(kn)).all()
+
+
 def test_iceberg_hot_key_contention():
     # every key repeated 64 times in one batch: CAS races on the same slots
     t = cht().Table(cht().ICEBERG, 40, 1 << 6, 1 << 3, seed=4)
@@ -293,24 +344,25 @@ def test_iceberg_hot_key_contention():
     _fop_contract(t, keys.numpy().astype(np.uint64), st, o.enumerate())
 
 
-def test_bounded_retry_runs_out_and_reports_error():
+@pytest.mark.parametrize("P", [1, 4])
+def test_bounded_retry_runs_out_and_reports_error(P):
     # One primary and one secondary bucket (16 + 16 slots of 64 bits for
     # 32-bit keys) and 64 distinct keys: in every round the tiles of a warp
     # race for the same first empty slot and all but one lose. With
     # retry_limit = 1 a key that loses twice gives up: CHT_ERROR status, the
     # table's error word set, and the kernel returns normally (no hang, no
     # trap). The keys that did get an answer follow Algorithm 1.
-    P = cht()
+    M = cht()
     keys = W.to_u32(W.unique_keys(0, 64, 32, 9))
-    t = P.Table(P.ICEBERG, 32, 1, 1, key_bytes=4, retry_limit=1, seed=3)
+    t = M.Table(M.ICEBERG, 32, 1, 1, key_bytes=4, retry_limit=1, seed=3, lookups_in_flight=P)
     st = t.find_or_put(keys.to(DEV)).cpu().numpy()
-    assert (st == P.ERROR).sum() > 0, np.bincount(st)
-    assert ((st == P.ERROR) | (st == P.PUT) | (st == P.FULL)).all()
+    assert (st == M.ERROR).sum() > 0, np.bincount(st)
+    assert ((st == M.ERROR) | (st == M.PUT) | (st == M.FULL)).all()
     assert t.error_flags() != 0
     stored, cnt = t.enumerate()
     kn = u64(keys)
-    assert cnt == (st == P.PUT).sum()
-    assert set(u64(stored).tolist()) == set(kn[st == P.PUT].tolist())
+    assert cnt == (st == M.PUT).sum()
+    assert set(u64(stored).tolist()) == set(kn[st == M.PUT].tolist())
     d = dump_into(mirror(t), t)
     assert d.check_entries() == 0 and d.check_order_property() == 0 and d.check_prefix() == 0
     assert d.check_duplicates() == 0
@@ -318,10 +370,10 @@ def test_bounded_retry_runs_out_and_reports_error():
     # reached on the same race
     t.clear()
     assert t.error_flags() == 0
-    t2 = P.Table(P.ICEBERG, 32, 1, 1, key_bytes=4, seed=3)
+    t2 = M.Table(M.ICEBERG, 32, 1, 1, key_bytes=4, seed=3)
     st2 = t2.find_or_put(keys.to(DEV)).cpu().numpy()
-    assert (st2 != P.ERROR).all() and t2.error_flags() == 0
-    assert (st2 == P.PUT).sum() == 32 and (st2 == P.FULL).sum() == 32
+    assert (st2 != M.ERROR).all() and t2.error_flags() == 0
+    assert (st2 == M.PUT).sum() == 32 and (st2 == M.FULL).sum() == 32
 
 
 @pytest.mark.parametrize("compact", [True, False])
