@@ -82,20 +82,27 @@ class Request:
                     key_bits=key_bits, seed=seed)
 
 
-def form_wave(pending: list, budget: int, admit=None) -> tuple[list, list]:
+def form_wave(pending: list, budget: int, admit=None,
+              lookahead: int = 4096) -> tuple[list, list]:
     """Split the pending requests (in arrival order) into the next wave and
     the rest. Per table the wave takes a run of consecutive lookups or one
     write request, and no request is taken past an earlier one of its table
     that stays behind, so every table sees its requests in admission order.
-    The wave holds at most budget keys, but always at least one request.
+    The wave holds at most budget keys, but always at least one request;
+    the first request that would overflow the budget ends the wave, and
+    only the first `lookahead` pending requests are examined, so forming a
+    wave costs O(lookahead) however many requests are waiting.
 
     admit(r), if given, is asked for each request the wave could take: OK
     takes it (its resources are then reserved), REJECT drops it (it is in
     neither list; the caller has marked it), WAIT leaves it and every later
-    request for a later wave. Linear in the number of pending requests."""
+    request for a later wave."""
     wave, rest, used, taken = [], [], 0, {}
     blocked = set()  # tables with an earlier request left for a later wave
     for i, r in enumerate(pending):
+        if i >= lookahead or (wave and used + r.n > budget):
+            rest.extend(pending[i:])
+            return wave, rest
         kind = "r" if r.op == FIND else "w"
         cur = taken.get(r.table)
         fits = used + r.n <= budget or not wave

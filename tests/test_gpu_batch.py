@@ -194,7 +194,7 @@ def test_packing_tuner_times_densest_and_wider(tmp_path, monkeypatch):
     monkeypatch.setenv("CHT_TUNE_CACHE", str(tmp_path / "tune.json"))
     import oracle
     from paper_2406_09255_gb300.tune import packing_candidates, tune_packing
-    w, nb0, nb1 = 48, 1 << 12, 1 << 9
+    w, nb0, nb1 = 38, 1 << 12, 1 << 9  # 26 + 1 and 29 + 2 bits: 2 or 1 fields per level
     keys = W.unique_keys(0, 40000, w, 515)
     keys = torch.cat([keys, keys[:10000]]).to(DEV)
     r = tune_packing(1, w, nb0, nb1, keys, "find_or_put", reps=1, seed=5)
