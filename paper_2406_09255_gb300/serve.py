@@ -18,7 +18,11 @@ Admission is by device memory and by table headroom:
     than the whole arena is rejected;
   - a write request reserves its fresh keys against its table's headroom (a
     share of the table's slots, max_fill) when it is admitted; one whose fresh
-    keys exceed the headroom left is rejected (a table never frees slots).
+    keys exceed the headroom left is rejected (a table never frees slots);
+  - a request with a deadline that is still waiting when the deadline passes
+    is cancelled (not run), e.g. one held back for memory too long.
+The arena's size is halved when the device cannot allocate it (alloc_arena).
+Each wave is an NVTX range, so a profiler's timeline shows the waves.
 Admitted requests get their keys generated on the device into their arena
 space (one generator launch per wave, from each request's key recipe), so the
 device holds only the keys of admitted requests.
@@ -62,6 +66,7 @@ class Request:
     n: int
     arrival: float          # seconds from the start of the run
     requery_frac: float = 0.4
+    deadline: float = -1.0  # give up if not admitted by then (seconds; < 0: never)
     # key recipe (Server.plan)
     n_fresh: int = 0
     fresh_base: int = 0
@@ -71,7 +76,7 @@ class Request:
     # filled in by the server
     admitted: float = -1.0
     done: float = -1.0
-    rejected: str = ""
+    rejected: str = ""      # why it was not served: headroom, size, cancelled
     off: int = -1           # position of the request's keys in the key arena
     keys: torch.Tensor | None = None    # kept with keep_results
     status: torch.Tensor | None = None  # kept with keep_results
@@ -188,6 +193,22 @@ class TableState:
     absent_base: int = 1 << 40
 
 
+def alloc_arena(keys: int, device, min_keys: int = 1 << 20, alloc=torch.empty):
+    """The key arena's buffers (int64 keys, uint8 statuses) for `keys`
+    positions; when the device runs out of memory, half as many, down to
+    min_keys (below that the error propagates). Returns (keys, statuses)."""
+    n = keys
+    while True:
+        try:
+            k = alloc(n, dtype=torch.int64, device=device)
+            st = alloc(n, dtype=torch.uint8, device=device)
+            return k, st
+        except torch.cuda.OutOfMemoryError:
+            if n // 2 < min_keys:
+                raise
+            n //= 2
+
+
 class Server:
     """Continuous-batching request loop over resident iceberg tables."""
 
@@ -204,9 +225,8 @@ class Server:
         if arena_keys is None:
             free, _ = torch.cuda.mem_get_info(self.dev)
             arena_keys = int(min(1 << 28, hbm_fraction * free / 9))  # 8 B key + 1 B status
-        self.arena = KeyArena(arena_keys)
-        self.keys = torch.empty(arena_keys, dtype=torch.int64, device=self.dev)
-        self.status = torch.empty(arena_keys, dtype=torch.uint8, device=self.dev)
+        self.keys, self.status = alloc_arena(arena_keys, self.dev)
+        self.arena = KeyArena(self.keys.numel())
         self.max_wave_keys = max_wave_keys
         self.keep_results = keep_results
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(2)]
@@ -247,7 +267,9 @@ class Server:
     # -- admission -------------------------------------------------------------
     def _admit(self, r: Request, now: float) -> str:
         st = self.states[r.table]
-        if r.op != FIND and r.n_fresh > st.limit - st.reserved:
+        if 0 <= r.deadline < now:
+            r.rejected = "cancelled"
+        elif r.op != FIND and r.n_fresh > st.limit - st.reserved:
             r.rejected = "table headroom"
         elif r.n > self.arena.cap:
             r.rejected = "larger than the key arena"
@@ -332,6 +354,13 @@ class Server:
             W.request_keys_device(span, self.keys, stream)
 
     def _issue(self, wave, slot, inflight):
+        torch.cuda.nvtx.range_push(f"wave {self.waves}: {len(wave)} requests")
+        try:
+            self._issue_wave(wave, slot, inflight)
+        finally:
+            torch.cuda.nvtx.range_pop()
+
+    def _issue_wave(self, wave, slot, inflight):
         s = self.streams[slot]
         writes = {r.table for r in wave if r.op != FIND}
         touched = {r.table for r in wave}

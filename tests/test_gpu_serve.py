@@ -92,7 +92,8 @@ def test_admission_by_memory_and_headroom():
     """A 6,000-key arena: a request that does not fit next to the one in
     flight waits (and so does the request behind it) and is admitted once the
     first completes; a write request whose fresh keys exceed its table's
-    headroom (max_fill = 0.3 of its slots) is rejected. Every admitted
+    headroom (max_fill = 0.3 of its slots) is rejected; a request whose
+    deadline has passed when it is considered is cancelled. Every admitted
     request's result equals the one-at-a-time run's and the oracle's."""
     from paper_2406_09255_gb300.serve import FIND, FOP, Request, Server, run_sequential
     nt = 3
@@ -101,7 +102,7 @@ def test_admission_by_memory_and_headroom():
     def requests():
         return [Request(0, 0, FOP, 4000, 0.0), Request(1, 1, FOP, 3000, 0.0),
                 Request(2, 2, FIND, 500, 0.0), Request(3, 0, FOP, 20000, 0.0),
-                Request(4, 2, FOP, 800, 0.0)]
+                Request(4, 2, FOP, 800, 0.0), Request(5, 1, FIND, 100, 0.0, deadline=0.0)]
 
     ta, tb = make_tables(nt, seeds), make_tables(nt, seeds)
     srv = Server(ta, seeds, keep_results=True, fill_cap=0.9, max_fill=0.3, arena_keys=6000)
@@ -111,7 +112,9 @@ def test_admission_by_memory_and_headroom():
     assert 1 in srv.held_for_memory
     assert r[1].admitted >= r[0].done and r[2].admitted >= r[0].done
     assert r[3].rejected == "table headroom" and r[3].status is None
-    assert srv.rejected == 1 and srv.arena.used() == 0
+    # a request whose deadline passed before it could be admitted is cancelled
+    assert r[5].rejected == "cancelled" and r[5].status is None
+    assert srv.rejected == 2 and srv.arena.used() == 0
     base = Server(tb, seeds, keep_results=True, fill_cap=0.9, max_fill=0.3)
     rb = {q.rid: q for q in run_sequential(base, base.plan(requests(), seed=5), realtime=False)}
     assert rb[3].rejected == "table headroom"

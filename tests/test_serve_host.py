@@ -118,3 +118,42 @@ def test_request_keys_definition():
     assert idx.tolist() == [7, 8, 1000, 1001, 1002]
     k = W.request_keys(10, 3, 100, 12345, 777, 1 << 40, 48, 99)
     assert k.tolist() == W.keys_at(torch.tensor(want), 48, 99).tolist()
+
+
+def test_arena_allocation_halves_on_out_of_memory():
+    from paper_2406_09255_gb300.serve import alloc_arena
+    tried = []
+
+    def fake_alloc(n, dtype, device):
+        tried.append(n)
+        if n > 1000:
+            raise torch.cuda.OutOfMemoryError("fake")
+        return torch.empty(n, dtype=dtype, device=device)
+
+    k, st = alloc_arena(8000, "cpu", min_keys=100, alloc=fake_alloc)
+    assert k.numel() == st.numel() == 1000 and k.dtype == torch.int64
+    assert tried[:4] == [8000, 4000, 2000, 1000]
+    try:
+        alloc_arena(8000, "cpu", min_keys=4000, alloc=fake_alloc)
+        assert False, "below the minimum the error propagates"
+    except torch.cuda.OutOfMemoryError:
+        pass
+
+
+def test_deadline_cancels_a_waiting_request():
+    """A request still waiting past its deadline is dropped as cancelled
+    when it is next considered (the host rule; the GPU test runs it)."""
+    from paper_2406_09255_gb300.serve import OK, REJECT, WAIT
+    p = reqs([(0, FOP, 10), (1, FIND, 10)])
+    p[1].deadline = 0.5
+    calls = []
+
+    def admit(r, now=1.0):
+        calls.append(r.rid)
+        if 0 <= r.deadline < now:
+            r.rejected = "cancelled"
+            return REJECT
+        return OK
+
+    wave, rest = form_wave(p, 10 ** 9, admit)
+    assert [r.rid for r in wave] == [0] and rest == [] and p[1].rejected == "cancelled"
