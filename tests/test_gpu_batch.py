@@ -214,3 +214,44 @@ def test_packing_tuner_times_densest_and_wider(tmp_path, monkeypatch):
     assert (puts == 1).all()
     r2 = tune_packing(1, w, nb0, nb1, keys, "find_or_put", reps=1, seed=5)
     assert r2["cached"] and r2["fields_per_word"] == r["fields_per_word"]
+
+
+def test_config4_full_shape_fused_and_graph_replay():
+    """The benchmark's 256-table batch at full shape (primary 2^8..2^18
+    buckets, secondary 1/8, 32-bit keys, log-uniform 1K..1M-key batches with
+    30 % duplicates), built exactly as the benchmark builds it, through one
+    fused launch and then, from empty tables again, one CUDA-graph replay.
+    Every table: one PUT per distinct key, the rest FOUND; a sample of
+    tables (all with 2^17 or more primary buckets, and every eighth other
+    one) is checked against the oracle's sequential replay (stored set) and
+    Theorem 1's invariants on the dump."""
+    from paper_2406_09255_gb300.batch import Batch
+    m = P()
+    spec = W.multi_table_spec()
+    assert len(spec) == 256 and max(e for e, _, _ in spec) == 18
+    tables, keys = [], []
+    for i, (e, size, distinct) in enumerate(spec):
+        tables.append(m.Table(m.ICEBERG, 32, 1 << e, 1 << (e - 3), key_bytes=4,
+                              fields_per_word=2, seed=4000 + i))
+        keys.append(W.to_u32(W.duplicate_stream(size, distinct, 32, W.SEED_BASE + 4 + 7 * i,
+                                                0.3, device=DEV)))
+    sample = [i for i, (e, _, _) in enumerate(spec) if e >= 17 or i % 8 == 0]
+    assert any(spec[i][0] == 18 for i in sample)
+    b = Batch(tables, keys)
+    for mode in ("fused", "graph"):
+        b.clear()
+        if mode == "fused":
+            b.launch()
+        else:
+            b.capture()
+            b.replay()
+        torch.cuda.synchronize()
+        for i, (t, k, s) in enumerate(zip(tables, keys, b.statuses)):
+            st = s.cpu().numpy()
+            assert ((st == m.PUT) | (st == m.FOUND)).all(), (mode, i)
+            kn = u64(k)
+            if len(kn):
+                uniq, inv = np.unique(kn, return_inverse=True)
+                assert (np.bincount(inv, weights=(st == m.PUT), minlength=len(uniq)) == 1).all()
+            if i in sample:
+                check_table(t, k, s)
