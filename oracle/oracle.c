@@ -765,15 +765,20 @@ uint64_t orc_check_order_property(const orc_cfg *c, const uint64_t *t0,
                     continue;
                 int x;
                 uint64_t k = orc_decode(c, level, a, e, &x);
+                /* k's three buckets and its entry for each */
+                uint64_t kb[3], ke[3];
+                for (int x2 = 0; x2 < 3; x2++) {
+                    kb[x2] = orc_iceberg_bucket(c, x2, k);
+                    ke[x2] = orc_iceberg_entry(c, x2, k);
+                }
                 int violated = 0;
                 for (int x2 = 0; x2 < 3 && !violated; x2++)
                     for (int y2 = 0; y2 < Bx[x2]; y2++) {
                         if (!orc_prec(x2, y2, x, y))
                             continue;
                         uint64_t e2 = orc_get_slot(
-                            c, x2 ? 1 : 0, orc_level_table(x2, t0, t1),
-                            orc_iceberg_bucket(c, x2, k), y2);
-                        if (e2 == 0 || e2 == orc_iceberg_entry(c, x2, k)) {
+                            c, x2 ? 1 : 0, orc_level_table(x2, t0, t1), kb[x2], y2);
+                        if (e2 == 0 || e2 == ke[x2]) {
                             violated = 1;
                             break;
                         }

@@ -221,10 +221,11 @@ def test_config4_full_shape_fused_and_graph_replay():
     buckets, secondary 1/8, 32-bit keys, log-uniform 1K..1M-key batches with
     30 % duplicates), built exactly as the benchmark builds it, through one
     fused launch and then, from empty tables again, one CUDA-graph replay.
-    Every table: one PUT per distinct key, the rest FOUND; a sample of
-    tables (all with 2^17 or more primary buckets, and every eighth other
-    one) is checked against the oracle's sequential replay (stored set) and
-    Theorem 1's invariants on the dump."""
+    Every table, both times: one PUT per distinct key, the rest FOUND. The
+    graph replay stores the same set in every table as the fused launch. A
+    sample of tables (the four largest batches into 2^18-bucket tables and
+    every 32nd table) is checked against the oracle's sequential replay
+    (stored set) and Theorem 1's invariants on the dump."""
     from paper_2406_09255_gb300.batch import Batch
     m = P()
     spec = W.multi_table_spec()
@@ -235,9 +236,10 @@ def test_config4_full_shape_fused_and_graph_replay():
                               fields_per_word=2, seed=4000 + i))
         keys.append(W.to_u32(W.duplicate_stream(size, distinct, 32, W.SEED_BASE + 4 + 7 * i,
                                                 0.3, device=DEV)))
-    sample = [i for i, (e, _, _) in enumerate(spec) if e >= 17 or i % 8 == 0]
-    assert any(spec[i][0] == 18 for i in sample)
+    big = sorted((i for i, (e, _, _) in enumerate(spec) if e == 18), key=lambda i: -spec[i][1])
+    sample = sorted(set(big[:4]) | set(range(0, 256, 32)))
     b = Batch(tables, keys)
+    stored = {}
     for mode in ("fused", "graph"):
         b.clear()
         if mode == "fused":
@@ -253,5 +255,10 @@ def test_config4_full_shape_fused_and_graph_replay():
             if len(kn):
                 uniq, inv = np.unique(kn, return_inverse=True)
                 assert (np.bincount(inv, weights=(st == m.PUT), minlength=len(uniq)) == 1).all()
-            if i in sample:
-                check_table(t, k, s)
+            got = torch.sort(t.enumerate()[0])[0]
+            if mode == "fused":
+                stored[i] = got
+                if i in sample:
+                    check_table(t, k, s)
+            else:
+                assert torch.equal(got, stored[i]), i

@@ -51,9 +51,9 @@ MUTATIONS = [
     ("order-property checker never visits the secondary level",
      "for (int level = 0; level < 2; level++) {", "for (int level = 0; level < 1; level++) {"),
     ("order-property checker misses a preceding copy of the same key",
-     "if (e2 == 0 || e2 == orc_iceberg_entry(c, x2, k)) {", "if (e2 == 0) {"),
+     "if (e2 == 0 || e2 == ke[x2]) {", "if (e2 == 0) {"),
     ("order-property checker looks in the wrong bucket",
-     "orc_iceberg_bucket(c, x2, k), y2);", "orc_iceberg_bucket(c, x, k), y2);"),
+     "kb[x2] = orc_iceberg_bucket(c, x2, k);", "kb[x2] = orc_iceberg_bucket(c, x, k);"),
     ("chain checker also inspects the entry's own bucket",
      "for (int jj = 0; jj < j; jj++)", "for (int jj = 0; jj <= j; jj++)"),
     ("chain checker skips the first bucket of the chain",
