@@ -343,7 +343,10 @@ int cht_set_counters(cht_table *t, cht_counters *d_counters);
 
 /*
  * Read the device error word of the table header (synchronises stream). A
- * nonzero value means some key got CHT_ERROR status since the last clear.
+ * nonzero value means something went wrong since the last clear: bit 0, some
+ * key got CHT_ERROR status (a bounded retry loop gave up); bit 1, a kernel's
+ * own bound on its loop ran out, and keys it had not answered may be left
+ * with CHT_ERROR or unwritten statuses. Neither happens in a correct run.
  */
 int cht_error_flags(const cht_table *t, uint32_t *flags, void *stream);
 

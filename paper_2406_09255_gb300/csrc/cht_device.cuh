@@ -36,6 +36,10 @@ constexpr uint8_t ST_NOT_FOUND = 0, ST_FOUND = 1, ST_PUT = 2, ST_FULL = 3,
 // level-1 step found its primary bucket full and that awaits level 2
 constexpr uint8_t ST_PENDING = 6;
 
+// bits of the table header's error word: a key reported ST_ERROR (a bounded
+// retry loop gave up), or a kernel's loop bound ran out
+constexpr uint32_t kErrRetry = 1u, kErrLoopBound = 2u;
+
 // One level of a table (cuckoo table, iceberg primary or iceberg secondary).
 struct Level {
     uint64_t *words;  // bucket b starts at words + 16 * b

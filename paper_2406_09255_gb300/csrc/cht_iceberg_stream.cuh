@@ -62,7 +62,18 @@ __global__ void __launch_bounds__(256, LOOKUP ? 3 : 2)
     uint64_t cur = 0, idx = 0;
     int it = 0;
     bool live = false;
+    // a bound on the rounds this warp can need: every round takes one step
+    // of each live key and a key takes at most max_iter + 1 steps; past it
+    // the warp records kErrLoopBound and stops, leaving its remaining keys'
+    // statuses unwritten
+    const uint64_t warp_keys = (n + stride - 1) / stride * 32 + 64;
+    const uint64_t max_rounds = warp_keys * (uint64_t)(max_iter + 2) + 64;
+    uint64_t rounds = 0;
     while (true) {
+        if (++rounds > max_rounds) {
+            if (lane == 0) atomicOr(ta.err, kErrLoopBound);
+            break;
+        }
         // refill the lanes without a key, in rank order
         const uint32_t need = __ballot_sync(0xffffffffu, !live);
         if (need) {

@@ -143,7 +143,22 @@ __device__ __forceinline__ void iceberg_warp(const Src &src, unsigned long long 
         bool any_pending = false;
 #pragma unroll
         for (int i = 0; i < I; ++i) any_pending |= pending[i];
+        // every pass resolves each pending key or counts one of its lost
+        // claims (at most max_iter per level, two levels and the stash), so
+        // 2 * max_iter + 8 passes bound a chunk; past that the keys still
+        // pending report ST_ERROR and kErrLoopBound is recorded
+        int passes = 0;
         while (__any_sync(0xffffffffu, any_pending)) {
+            if (++passes > 2 * max_iter + 8) {
+#pragma unroll
+                for (int i = 0; i < I; ++i)
+                    if (pending[i]) {
+                        st[i] = ST_ERROR;
+                        pending[i] = false;
+                    }
+                if (lane == 0) atomicOr(ta.err, kErrLoopBound);
+                break;
+            }
             // ---- level-1 pass: the primary bucket of every key still at level 1
             uint32_t pm[I];
             bool more = false;
