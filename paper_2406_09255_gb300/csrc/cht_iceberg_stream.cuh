@@ -179,24 +179,30 @@ __global__ void __launch_bounds__(256, LOOKUP ? 3 : 2)
                 }
                 if (on && tl == s) {
                     n_probe++;
-                    uint8_t done = 0;  // status once the level-1 step has ended
+                    // the level-1 step's outcome; fin: the key leaves this
+                    // kernel (ST_NOT_FOUND is 0, so the status alone cannot
+                    // say whether the step has ended)
+                    bool fin = true;
+                    uint8_t out = ST_NOT_FOUND;
                     if (bm) {
-                        done = ST_FOUND;
+                        out = ST_FOUND;
                     } else if (!be) {
-                        done = ST_PENDING;  // primary full: level 2
+                        out = ST_PENDING;  // primary full: level 2
                     } else if (LOOKUP) {
-                        done = ST_NOT_FOUND;
+                        out = ST_NOT_FOUND;  // the primary has room and no k
                     } else if (outcome == 1) {
-                        done = ST_PUT;
+                        out = ST_PUT;
                         n_write++;
                     } else if (outcome == 2) {
-                        done = ST_FOUND;  // another thread put k first
+                        out = ST_FOUND;  // another thread put k first
                     } else if (++it > max_iter) {
-                        done = ST_ERROR;
-                        atomicOr(ta.err, 1u);
+                        out = ST_ERROR;
+                        atomicOr(ta.err, kErrRetry);
+                    } else {
+                        fin = false;  // lost the claim to another key: next round
                     }
-                    if (done) {
-                        status[idx] = done;
+                    if (fin) {
+                        status[idx] = out;
                         live = false;
                     }
                 }
