@@ -542,8 +542,9 @@ def run_iceberg_stream(args, dev):
     """Compact iceberg, 48-bit keys, 2^22 primary + 2^19 secondary buckets
     (32 slots each): a find-or-put stream (80 % find-or-put, 20 % lookups,
     half of the keys first-seen, half Zipf(0.99) repeats over seen keys by
-    recency) run in stream-order batches of 2^22 ops until the distinct keys
-    reach 0.9 of the slots."""
+    recency) run in stream-order batches of 2^24 ops until the distinct keys
+    reach 0.9 of the slots. Within a batch the find-or-puts run as one
+    concurrent launch, then the lookups."""
     from paper_2406_09255_gb300 import ICEBERG, Table
     from paper_2406_09255_gb300 import workloads as W
     t = Table(ICEBERG, 48, 1 << 22, 1 << 19, seed=3000, device=dev)
@@ -552,7 +553,7 @@ def run_iceberg_stream(args, dev):
     n_ops = min(500_000_000, int(max_distinct / 0.4 * 1.02))
     keys, is_find, seen = W.fop_stream(n_ops, 48, W.SEED_BASE + 3, max_distinct=max_distinct,
                                        rng_seed=3, device=dev)
-    B = 1 << 22
+    B = 1 << 24
     batches = []
     for s0 in range(0, n_ops, B):
         k, f = keys[s0:s0 + B], is_find[s0:s0 + B]
@@ -595,23 +596,35 @@ def run_iceberg_stream(args, dev):
     ctr = t.attach_counters()
     step()
     torch.cuda.synchronize()
-    probes, writes, _, ops = [int(x) for x in ctr.tolist()]
+    probes, writes, fails, ops = [int(x) for x in ctr.tolist()]
     t.detach_counters()
     peak, pk = peaks()
     byt = 128.0 * probes + 32.0 * writes + 9.0 * ops
     ach = byt / (ms / args.steps * 1e-3) / 1e9
-    out = {"metric": "Mops/s find-or-put stream vs fill factor", "value": n_ops * args.steps / ms / 1e3,
+    # the access-pattern ceiling of this op mix: each compare-and-swap (won
+    # or lost) at the measured put rate, every other probe at the measured
+    # random-line read rate
+    rd, cl = random_read_ceiling(dev), random_claim_ceiling(dev)
+    cas = (writes + fails) / ops
+    reads = max(probes - writes - fails, 0) / ops
+    ceil_mops = 1.0 / (cas / cl + reads / rd) / 1e6
+    value = n_ops * args.steps / ms / 1e3
+    out = {"metric": "Mops/s find-or-put stream vs fill factor", "value": value,
            "unit": "Mops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": "u64",
            "data": "synthetic",
            "config": {"workload": f"iceberg_stream: compact iceberg w=48, 2^22 x 32 + 2^19 x 32 "
                                   f"slots ({slots}), {n_ops} ops (80% find-or-put / 20% find, 50% "
-                                  f"Zipf(0.99) repeats), batches of 2^22 ops, fill 0 -> 0.9"},
+                                  f"Zipf(0.99) repeats), batches of 2^24 ops, fill 0 -> 0.9"},
            "bands_mops": {k: v[0] / v[1] / 1e3 for k, v in sorted(bands.items())},
            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                         "frac": ach / peak, "peak_source": f"{pk} hbm_gbs",
                         "bytes_model": "128 B per probe + 32 B per slot write + 9 B per op"},
+           "access_ceiling": {"cas_per_op": cas, "plain_probes_per_op": reads,
+                              "random_read_lines_per_s": rd, "random_claim_lines_per_s": cl,
+                              "ceiling_mops": ceil_mops, "frac": value / ceil_mops},
            "probes_per_op": probes / ops, "writes_per_op": writes / ops,
+           "failed_claims_per_op": fails / ops,
            "final_fill": int(t.enumerate()[1]) / slots, "clocks": clk}
     return out
 
@@ -958,7 +971,8 @@ def run_served(args, dev, rates=(0.25, 0.5, 0.9, 1.2, 1.5, 2.0)):
 def run_profile_case(kind: str, dev):
     """Small case for ncu captures (a few GB on the device): the 2^24-bucket
     compact cuckoo table filled to 0.8 (or a 2^22 + 2^19 iceberg table to
-    0.6), then three launches of one kernel over 2^24 keys."""
+    0.6), then three launches of one kernel over 2^24 keys; or three fused
+    launches of the 256-table batch."""
     from paper_2406_09255_gb300 import CUCKOO, ICEBERG, Table
     from paper_2406_09255_gb300 import workloads as W
     m = 1 << 24
@@ -980,16 +994,38 @@ def run_profile_case(kind: str, dev):
         else:
             for i in range(3):
                 t.insert(W.unique_keys(pre + i * m, m, 40, seed, device=dev), status=st)
-    else:
+    elif kind in ("fop", "ifind"):
         seed = W.SEED_BASE + 3
         t = Table(ICEBERG, 48, 1 << 22, 1 << 19, seed=3000, device=dev)
         n = int(0.6 * t.slots)
-        t.find_or_put(W.unique_keys(0, n - 3 * m, 48, seed, device=dev))
+        pre = n - 3 * m if kind == "fop" else n
+        t.find_or_put(W.unique_keys(0, pre, 48, seed, device=dev))
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        for i in range(3):
-            k = W.unique_keys(n - 3 * m + i * m // 2, m, 48, seed, device=dev)  # half repeats
-            t.find_or_put(k, status=st)
+        if kind == "fop":
+            for i in range(3):
+                k = W.unique_keys(n - 3 * m + i * m // 2, m, 48, seed, device=dev)  # half repeats
+                t.find_or_put(k, status=st)
+        else:
+            q, _ = W.find_queries(n, m, 0.5, 48, seed, n, device=dev)
+            for _ in range(3):
+                t.find(q, status=st)
+    else:
+        # the 256-table fused find-or-put (2^8..2^18 primary buckets, 32-bit
+        # keys, 30 % duplicates): three launches, each from empty tables
+        from paper_2406_09255_gb300.batch import Batch
+        spec = W.multi_table_spec()
+        tables, keys = [], []
+        for i, (e, size, distinct) in enumerate(spec):
+            tables.append(Table(ICEBERG, 32, 1 << e, 1 << (e - 3), key_bytes=4,
+                                fields_per_word=2, seed=4000 + i, device=dev))
+            keys.append(W.to_u32(W.duplicate_stream(size, distinct, 32, W.SEED_BASE + 4 + 7 * i,
+                                                    0.3, device=dev)))
+        b = Batch(tables, keys)
+        b.set_launch(tile=4, items_per_thread=1)
+        for _ in range(3):
+            b.clear()
+            b.launch()
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": kind, "ok": True,
                       "max_gib": torch.cuda.max_memory_allocated(dev) / 2 ** 30}))
@@ -1096,7 +1132,7 @@ def main():
                          "256-table batch, served loop) that follow the headline")
     ap.add_argument("--requests", type=int, default=100000,
                     help="served workload: request count")
-    ap.add_argument("--profile", choices=["find", "insert", "fop"],
+    ap.add_argument("--profile", choices=["find", "insert", "fop", "ifind", "batch"],
                     help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile:
