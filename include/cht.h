@@ -363,8 +363,10 @@ int cht_error_flags(const cht_table *t, uint32_t *flags, void *stream);
  *
  * All tables of a batch must be iceberg tables on the current device with the
  * same primary packing (fields_per_word). Tables, key arrays and status arrays
- * must stay alive, and no table may appear twice, for as long as the batch is
- * launched. A table may be written by only one batch or call at a time.
+ * must stay alive for as long as the batch is launched. In a find-or-put batch
+ * no table may appear twice (CHT_ERR_INVALID); a lookup batch may list a table
+ * several times, each entry with its own keys (lookups only read). A table may
+ * be written by only one batch or call at a time.
  */
 typedef struct cht_batch cht_batch; /* opaque host handle */
 

@@ -18,7 +18,8 @@ OP_FIND = 1
 class Batch:
     """One operation over many (table, keys) pairs in a single kernel launch.
 
-    tables: list of iceberg Table objects (same primary packing, no repeats);
+    tables: list of iceberg Table objects (same primary packing; a table may
+    repeat only in a lookup batch);
     keys: list of device key tensors (each of its table's key dtype);
     statuses: optional list of uint8 device tensors (allocated if omitted).
     The descriptor scratch is a device tensor owned by this object.
@@ -37,6 +38,26 @@ class Batch:
             statuses = [torch.empty(k.numel(), dtype=torch.uint8, device=k.device)
                         for k in self.keys]
         self.statuses = statuses
+        self._create([k.data_ptr() for k in self.keys], [k.numel() for k in self.keys],
+                     [s.data_ptr() for s in self.statuses], stream)
+
+    @classmethod
+    def from_pointers(cls, tables, key_ptrs, counts, status_ptrs, op: int = OP_FIND_OR_PUT,
+                      stream=None):
+        """A batch over raw device addresses (key_ptrs[i]: counts[i] keys of
+        tables[i]'s key dtype; status_ptrs[i]: counts[i] bytes), for callers
+        that place many requests in one device buffer. The caller keeps that
+        memory alive while the batch is used; keys and statuses are not
+        held."""
+        b = cls.__new__(cls)
+        b._L = _lib.load()
+        b.op = op
+        b.tables = list(tables)
+        b.keys = b.statuses = None
+        b._create(list(key_ptrs), list(counts), list(status_ptrs), stream)
+        return b
+
+    def _create(self, key_ptrs, counts, status_ptrs, stream):
         count = len(self.tables)
         nbytes = int(self._L.cht_batch_scratch_bytes(count))
         if nbytes == 0:
@@ -44,13 +65,13 @@ class Batch:
         self.scratch = torch.empty(nbytes, dtype=torch.uint8, device=self.tables[0].device)
         vp = ctypes.c_void_p
         T = (vp * count)(*[t.handle for t in self.tables])
-        K = (vp * count)(*[k.data_ptr() for k in self.keys])
-        N = (ctypes.c_size_t * count)(*[k.numel() for k in self.keys])
-        S = (vp * count)(*[s.data_ptr() for s in self.statuses])
+        K = (vp * count)(*key_ptrs)
+        N = (ctypes.c_size_t * count)(*counts)
+        S = (vp * count)(*status_ptrs)
         self._h = vp()
-        check(self._L.cht_batch_create(T, K, N, S, count, op, self.scratch.data_ptr(), nbytes,
-                                       _stream_handle(stream), ctypes.byref(self._h)))
-        self.n_keys = sum(k.numel() for k in self.keys)
+        check(self._L.cht_batch_create(T, K, N, S, count, self.op, self.scratch.data_ptr(),
+                                       nbytes, _stream_handle(stream), ctypes.byref(self._h)))
+        self.n_keys = sum(counts)
 
     def set_launch(self, tile=0, items_per_thread=0, cta_threads=0, max_ctas=0):
         c = Config()

@@ -698,6 +698,15 @@ int cht_batch_create(cht_table *const *tables, const void *const *d_keys, const 
         b->host[i].n = n[i];
         b->host[i].status = d_status[i];
     }
+    if (op == CHT_OP_FIND_OR_PUT) {
+        // concurrent writes from two entries of one table would race
+        std::vector<const cht_table *> seen(tables, tables + count);
+        std::sort(seen.begin(), seen.end());
+        if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) {
+            delete b;
+            return fail(CHT_ERR_INVALID, "a find-or-put batch lists a table twice");
+        }
+    }
     // descriptors travel as kernel parameters (kDescPerLaunch per launch): the
     // upload is asynchronous and leaves no host buffer to keep alive
     cudaError_t ce = cudaSuccess;

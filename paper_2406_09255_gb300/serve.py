@@ -45,6 +45,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import heapq
 import time
 
 import numpy as np
@@ -87,45 +88,75 @@ class Request:
                     key_bits=key_bits, seed=seed)
 
 
-def form_wave(pending: list, budget: int, admit=None,
-              lookahead: int = 4096) -> tuple[list, list]:
-    """Split the pending requests (in arrival order) into the next wave and
-    the rest. Per table the wave takes a run of consecutive lookups or one
-    write request, and no request is taken past an earlier one of its table
-    that stays behind, so every table sees its requests in admission order.
-    The wave holds at most budget keys, but always at least one request;
-    the first request that would overflow the budget ends the wave, and
-    only the first `lookahead` pending requests are examined, so forming a
-    wave costs O(lookahead) however many requests are waiting.
+class PendingQueues:
+    """Requests waiting for a wave, one queue per table (each in arrival
+    order), and the wave-forming rule over them.
+
+    Per table a wave takes a run of consecutive lookups or one write
+    request, and never a request past an earlier one of its table that stays
+    behind, so every table sees its requests in admission order. Across
+    tables, the requests that could join (each table's next ones) are taken
+    in arrival order; the wave holds at most `budget` keys, but always at
+    least one request, and the first of those requests that would overflow
+    the budget ends the wave, as does reaching max_requests. Forming a wave
+    examines only the requests it takes plus one per table, however many are
+    waiting.
 
     admit(r), if given, is asked for each request the wave could take: OK
-    takes it (its resources are then reserved), REJECT drops it (it is in
-    neither list; the caller has marked it), WAIT leaves it and every later
-    request for a later wave."""
-    wave, rest, used, taken = [], [], 0, {}
-    blocked = set()  # tables with an earlier request left for a later wave
-    for i, r in enumerate(pending):
-        if i >= lookahead or (wave and used + r.n > budget):
-            rest.extend(pending[i:])
-            return wave, rest
-        kind = "r" if r.op == FIND else "w"
-        cur = taken.get(r.table)
-        fits = used + r.n <= budget or not wave
-        ok = fits and (cur is None or (cur == "r" and kind == "r"))
-        if ok and r.table not in blocked:
+    takes it (its resources are then reserved), REJECT drops it (the caller
+    has marked it), WAIT leaves it and ends the wave, so that no later
+    request overtakes one held back for memory."""
+
+    def __init__(self, requests=()):
+        self.q: dict[int, collections.deque] = {}
+        self.n = 0
+        for r in requests:
+            self.add(r)
+
+    def add(self, r: Request) -> None:
+        self.q.setdefault(r.table, collections.deque()).append(r)
+        self.n += 1
+
+    def __len__(self) -> int:
+        return self.n
+
+    def requests(self) -> list[Request]:
+        """Every waiting request, in arrival order."""
+        return sorted((r for q in self.q.values() for r in q), key=lambda r: (r.arrival, r.rid))
+
+    def form_wave(self, budget: int, admit=None, max_requests: int = 4096) -> list[Request]:
+        wave, used = [], 0
+        took: dict[int, str] = {}  # table -> "r" (took lookups) or "w" (took a write)
+        # the heap holds each table's next request while it may still join
+        heads = [(q[0].arrival, q[0].rid, t) for t, q in self.q.items() if q]
+        heapq.heapify(heads)
+        while heads:
+            _, _, t = heapq.heappop(heads)
+            q = self.q[t]
+            r = q[0]
+            if wave and (used + r.n > budget or len(wave) >= max_requests):
+                break
             verdict = admit(r) if admit is not None else OK
-            if verdict == REJECT:
-                continue
             if verdict == WAIT:
-                rest.extend(pending[i:])
-                return wave, rest
-            wave.append(r)
-            used += r.n
-            taken[r.table] = kind
-        else:
-            rest.append(r)
-            blocked.add(r.table)
-    return wave, rest
+                break
+            q.popleft()
+            self.n -= 1
+            if verdict != REJECT:
+                wave.append(r)
+                used += r.n
+                took[t] = "r" if r.op == FIND else "w"
+            k = took.get(t)
+            if q and (k is None or (k == "r" and q[0].op == FIND)):
+                heapq.heappush(heads, (q[0].arrival, q[0].rid, t))
+        return wave
+
+
+def form_wave(pending: list, budget: int, admit=None) -> tuple[list, list]:
+    """The wave rule of PendingQueues over a list in arrival order: returns
+    (wave, rest), rest being the requests not taken, in arrival order."""
+    pq = PendingQueues(pending)
+    wave = pq.form_wave(budget, admit)
+    return wave, pq.requests()
 
 
 class KeyArena:
@@ -293,7 +324,7 @@ class Server:
         requests with admitted/done times (and, with keep_results, their keys
         and statuses) filled in."""
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
-        pending: list[Request] = []
+        pending = PendingQueues()
         inflight = []   # (event, requests, write_tables, all_tables)
         nxt = 0
         t0 = time.perf_counter()
@@ -301,7 +332,7 @@ class Server:
         while nxt < len(reqs) or pending or inflight:
             now = time.perf_counter() - t0
             while nxt < len(reqs) and (not realtime or reqs[nxt].arrival <= now):
-                pending.append(reqs[nxt])
+                pending.add(reqs[nxt])
                 nxt += 1
             # retire finished waves
             still = []
@@ -323,8 +354,7 @@ class Server:
                         time.sleep(min(0.001, gap - 2e-4))
                 continue
             tnow = time.perf_counter() - t0
-            wave, pending = form_wave(pending, self.max_wave_keys,
-                                      lambda r: self._admit(r, tnow))
+            wave = pending.form_wave(self.max_wave_keys, lambda r: self._admit(r, tnow))
             if not wave:
                 continue  # held for memory (or all rejected): wait for a wave to finish
             for r in wave:
@@ -364,14 +394,17 @@ class Server:
         s = self.streams[slot]
         writes = {r.table for r in wave if r.op != FIND}
         touched = {r.table for r in wave}
-        # order after in-flight waves that conflict on a table with a write
-        for ev, rs, wt, at in inflight:
-            if (writes & at) or (wt & touched):
-                s.wait_event(ev)
         with torch.cuda.stream(s):
+            # the keys go into arena space that no in-flight wave uses, so
+            # their generation need not wait for anything
             self._generate(wave, s)
-            view = {r.rid: (self.keys[r.off: r.off + r.n], self.status[r.off: r.off + r.n])
-                    for r in wave}
+            # the table work waits for in-flight waves that conflict on a
+            # table with a write
+            for ev, rs, wt, at in inflight:
+                if (writes & at) or (wt & touched):
+                    s.wait_event(ev)
+            kbase, sbase = self.keys.data_ptr(), self.status.data_ptr()
+            kb = self.keys.element_size()
             finds = [r for r in wave if r.op == FIND and r.n]
             fops = [r for r in wave if r.op != FIND and r.n]
             for group, op in ((finds, OP_FIND), (fops, OP_FIND_OR_PUT)):
@@ -381,43 +414,26 @@ class Server:
                     # a lone request needs no fused plan: one direct launch
                     r = group[0]
                     t = self.states[r.table].table
-                    k, st = view[r.rid]
+                    k, st = self.keys[r.off: r.off + r.n], self.status[r.off: r.off + r.n]
                     if op == OP_FIND:
                         t.find(k, status=st, stream=s)
                     else:
                         t.find_or_put(k, status=st, stream=s)
                     self.launches += 1
                     continue
-                # one fused launch; several lookups of one table become one
-                # entry over their keys (lookups commute); their arena ranges
-                # are gathered into one key array
-                by_table: dict[int, list[Request]] = {}
-                for r in group:
-                    by_table.setdefault(r.table, []).append(r)
-                tabs, keys, sts, splits = [], [], [], []
-                for tid, rs in by_table.items():
-                    tabs.append(self.states[tid].table)
-                    if len(rs) == 1:
-                        k, st = view[rs[0].rid]
-                        keys.append(k)
-                        sts.append(st)
-                    else:
-                        keys.append(torch.cat([view[r.rid][0] for r in rs]))
-                        sts.append(torch.empty(sum(r.n for r in rs), dtype=torch.uint8,
-                                               device=self.dev))
-                        splits.append((sts[-1], rs))
-                b = Batch(tabs, keys, sts, op=op, stream=s)
+                # one fused launch with an entry per request, in place in the
+                # arena (a lookup batch may list a table several times; a
+                # wave holds at most one write request per table)
+                b = Batch.from_pointers([self.states[r.table].table for r in group],
+                                        [kbase + kb * r.off for r in group],
+                                        [r.n for r in group],
+                                        [sbase + r.off for r in group], op=op, stream=s)
                 b.launch(stream=s)
                 self.launches += 1
-                for big, rs in splits:
-                    off = 0
-                    for r in rs:
-                        view[r.rid][1].copy_(big[off: off + r.n])
-                        off += r.n
             if self.keep_results:
                 for r in wave:
-                    k, st = view[r.rid]
-                    r.keys, r.status = k.clone(), st.clone()
+                    r.keys = self.keys[r.off: r.off + r.n].clone()
+                    r.status = self.status[r.off: r.off + r.n].clone()
             ev = torch.cuda.Event()
             ev.record(s)
         self.waves += 1

@@ -18,6 +18,7 @@ and on the GPU and gives identical values.
 from __future__ import annotations
 
 import ctypes
+import functools
 import math
 import os
 
@@ -56,8 +57,9 @@ def splitmix(seed: int, idx: int) -> int:
     return mix64(seed + (idx + 1) * GAMMA)
 
 
-def _round_keys(seed: int) -> list[int]:
-    return [splitmix(seed ^ 0x5EED_0F_FE15, r) for r in range(4)]
+@functools.lru_cache(maxsize=4096)
+def _round_keys(seed: int) -> tuple[int, ...]:
+    return tuple(splitmix(seed ^ 0x5EED_0F_FE15, r) for r in range(4))
 
 
 def _feistel_scalar(x: int, bits: int, rk: list[int], inverse: bool) -> int:
@@ -125,6 +127,7 @@ def _bijection_t(x: torch.Tensor, w: int, seed: int) -> torch.Tensor:
     return y
 
 
+@functools.lru_cache(maxsize=4096)
 def key_index_skip(w: int, seed: int) -> int:
     """The one index i with G_s(i) = 0; it is skipped when numbering keys."""
     return g_scalar(0, w, seed, inverse=True)

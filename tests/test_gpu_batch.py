@@ -147,6 +147,38 @@ def test_batch_rejects_mixed_packing_and_cuckoo():
         Batch([a, c], [k, k])
 
 
+def test_lookup_batch_may_repeat_a_table_find_or_put_may_not():
+    """A lookup batch lists one table several times, each entry over its own
+    keys placed in one buffer (Batch.from_pointers), and answers each entry
+    as cht_find on that table; a find-or-put batch that lists a table twice
+    is refused."""
+    m = P()
+    from paper_2406_09255_gb300.batch import OP_FIND, Batch
+    tables, keys = make_tables(SPEC[:2], seed0=800)
+    for t, k in zip(tables, keys):
+        t.find_or_put(k)
+    w = 32
+    # half of each table's queries were put (its batch's distinct keys come
+    # first in the same key sequence)
+    q = [W.to_u32(W.unique_keys(lo, n, w, 800 + 7 * i)).to(DEV)
+         for i, lo, n in ((0, 2000, 3000), (1, 67500, 5000))]
+    # entries: table 0, table 1, table 0 again, table 1 again (one buffer)
+    parts = [q[0][:1000], q[1][:2000], q[0][1000:], q[1][2000:]]
+    buf = torch.cat(parts)
+    st = torch.full((buf.numel(),), 255, dtype=torch.uint8, device=DEV)
+    offs = np.cumsum([0] + [p.numel() for p in parts])[:-1]
+    tabs = [tables[0], tables[1], tables[0], tables[1]]
+    b = Batch.from_pointers(tabs, [buf.data_ptr() + 4 * int(o) for o in offs],
+                            [p.numel() for p in parts], [st.data_ptr() + int(o) for o in offs],
+                            op=OP_FIND)
+    b.launch()
+    want = torch.cat([t.find(p) for t, p in zip(tabs, parts)])
+    assert torch.equal(st, want)
+    assert int((want == m.FOUND).sum()) > 0 and int((want == m.NOT_FOUND).sum()) > 0
+    with pytest.raises(m.ChtError):
+        Batch([tables[0], tables[1], tables[0]], [keys[0], keys[1], keys[0]])
+
+
 def test_tuner_picks_a_valid_shape(tmp_path, monkeypatch):
     monkeypatch.setenv("CHT_TUNE_CACHE", str(tmp_path / "tune.json"))
     from paper_2406_09255_gb300.batch import Batch

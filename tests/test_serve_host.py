@@ -5,7 +5,8 @@ import random
 
 import torch
 
-from paper_2406_09255_gb300.serve import FIND, FOP, INSERT, Request, form_wave
+from paper_2406_09255_gb300.serve import (FIND, FOP, INSERT, OK, REJECT, WAIT, PendingQueues,
+                                          Request, form_wave)
 
 
 def reqs(spec):
@@ -57,8 +58,62 @@ def test_random_streams_keep_per_table_order_and_drain():
         assert ids == sorted(ids), "a table sees its requests in admission order"
 
 
+def _reference_wave(pending, budget, admit):
+    """The wave rule written as one plain pass over the requests in arrival
+    order (O(n)): a table closes once it took a write or left a request
+    behind; the first candidate over the budget, or one that must wait,
+    ends the wave."""
+    wave, rest, used, took, closed, stopped = [], [], 0, {}, set(), False
+    for r in pending:
+        if stopped or r.table in closed:
+            rest.append(r)
+            continue
+        if took.get(r.table) == "r" and r.op != FIND:
+            closed.add(r.table)
+            rest.append(r)
+            continue
+        if wave and used + r.n > budget:
+            stopped = True
+            rest.append(r)
+            continue
+        v = admit(r)
+        if v == WAIT:
+            stopped = True
+            rest.append(r)
+            continue
+        if v == REJECT:
+            continue
+        wave.append(r)
+        used += r.n
+        took[r.table] = "r" if r.op == FIND else "w"
+        if r.op != FIND:
+            closed.add(r.table)
+    return wave, rest
+
+
+def test_per_table_queues_match_the_plain_rule():
+    """The per-table queues take the same wave, and leave the same requests
+    in the same order, as the plain pass over every waiting request."""
+    rnd = random.Random(11)
+    for trial in range(400):
+        nt = rnd.randrange(1, 6)
+        spec = [(rnd.randrange(nt), rnd.choice([FIND, FIND, FOP, INSERT]), rnd.randrange(1, 50))
+                for _ in range(rnd.randrange(1, 120))]
+        budget = rnd.randrange(20, 400)
+        verdict = {i: rnd.choice([OK] * 12 + [REJECT, WAIT]) for i in range(len(spec))}
+        ref_wave, ref_rest = _reference_wave(reqs(spec), budget, lambda r: verdict[r.rid])
+        pq = PendingQueues(reqs(spec))
+        wave = pq.form_wave(budget, lambda r: verdict[r.rid])
+        assert [r.rid for r in wave] == [r.rid for r in ref_wave]
+        assert [r.rid for r in pq.requests()] == [r.rid for r in ref_rest]
+        assert len(pq) == len(ref_rest)
+    # a table that left a write behind takes none of its later lookups
+    p = reqs([(0, FOP, 5), (1, FIND, 3), (1, FOP, 4), (1, FIND, 1), (0, FIND, 1)])
+    wave, rest = form_wave(p, 10 ** 9)
+    assert [r.rid for r in wave] == [0, 1] and [r.rid for r in rest] == [2, 3, 4]
+
+
 def test_admission_wait_keeps_arrival_order_and_reject_drops():
-    from paper_2406_09255_gb300.serve import OK, REJECT, WAIT
     p = reqs([(0, FIND, 10), (1, FOP, 500), (2, FIND, 10), (3, FOP, 7)])
     verdicts = {0: OK, 1: WAIT, 2: OK, 3: OK}
     wave, rest = form_wave(p, 10 ** 9, lambda r: verdicts[r.rid])
