@@ -968,6 +968,20 @@ def run_served(args, dev, rates=(0.25, 0.5, 0.9, 1.2, 1.5, 2.0)):
     return out
 
 
+def warm_library(dev):
+    """One small find-or-put and lookup before anything is timed: the first
+    launch of the library in a process also pays one-time loading costs
+    (measured at ~18 ms), which would otherwise land in the first timed
+    launch."""
+    from paper_2406_09255_gb300 import ICEBERG, Table
+    from paper_2406_09255_gb300 import workloads as W
+    t = Table(ICEBERG, 32, 1 << 10, 1 << 7, key_bytes=4, fields_per_word=2, device=dev)
+    k = W.to_u32(W.unique_keys(0, 4096, 32, 1, device=dev))
+    t.find_or_put(k)
+    t.find(k)
+    torch.cuda.synchronize(dev)
+
+
 def run_profile_case(kind: str, dev):
     """Small case for ncu captures (a few GB on the device): the 2^24-bucket
     compact cuckoo table filled to 0.8 (or a 2^22 + 2^19 iceberg table to
@@ -1148,6 +1162,7 @@ def main():
         torch.cuda.set_device(dev)
         import __graft_entry__
         __graft_entry__.build()
+        warm_library(dev)
         print(json.dumps(others[args.workload](args, dev)))
         return 0
     spec = WORKLOADS[args.workload]
