@@ -280,6 +280,34 @@ def test_iceberg_fop_duplicates_parity(T, items):
     assert t.error_flags() == 0
 
 
+@pytest.mark.parametrize("T,items", [(4, 1), (8, 2), (16, 4)])
+def test_iceberg_copies_within_a_chunk(T, items):
+    """Copies of a key next to each other, so that they race inside one
+    warp's chunk: exactly one PUT per distinct key, the other copies FOUND,
+    the oracle's stored set, and lookups whose copies all agree with
+    membership."""
+    w = 40
+    t = cht().Table(cht().ICEBERG, w, 1 << 12, 1 << 9, seed=29, tile=T, items_per_thread=items)
+    o = mirror(t)
+    n = int(0.6 * t.slots)
+    fresh = W.unique_keys(0, n, w, 61)
+    rng = np.random.default_rng(61)
+    # each key 1-6 times, copies placed next to each other
+    reps = rng.integers(1, 7, n)
+    keys = torch.from_numpy(np.repeat(fresh.numpy(), reps))
+    st = t.find_or_put(keys.to(DEV)).cpu().numpy()
+    kn = keys.numpy().astype(np.uint64)
+    ost = o.insert(kn)
+    assert (ost != oracle.FULL).all()
+    _fop_contract(t, kn, st, o.enumerate())
+    # lookups: present and absent keys, each in runs of copies
+    q = torch.from_numpy(np.repeat(W.unique_keys(n - 2000, 4000, w, 61).numpy(), 5))
+    got = t.find(q.to(DEV)).cpu().numpy()
+    assert (o.find(q.numpy().astype(np.uint64)) == got).all()
+    assert (got == cht().FOUND).sum() == 5 * 2000 and (got == cht().NOT_FOUND).sum() == 5 * 2000
+    assert t.error_flags() == 0
+
+
 @pytest.mark.parametrize("T,P", [(4, 4), (8, 4), (4, 8), (16, 8)])
 def test_iceberg_stream_form_parity(T, P):
     """The stream form (level 1 in packed rounds with P loads in flight per
