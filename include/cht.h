@@ -436,7 +436,8 @@ int cht_batch_destroy(cht_batch *b);
  * streams, or different host threads) race: order them on one stream.
  * Arguments and per-key results are as for cht_batch_create /
  * cht_find_or_put; all tables must be iceberg tables with the same primary
- * packing on the current device.
+ * packing on the current device, and no table may be listed twice
+ * (CHT_ERR_INVALID).
  */
 #define CHT_STATIC_BATCH_MAX 256
 int cht_batch_find_or_put_static(cht_table *const *tables, const void *const *d_keys,

@@ -914,6 +914,15 @@ extern "C" int cht_batch_find_or_put_static(cht_table *const *tables, const void
             return fail(CHT_ERR_INVALID, "keys of batch entry %d not aligned", i);
         total_chunks += (n[i] + per - 1) / per;
     }
+    {
+        // a table listed twice would have its writes race (as in
+        // cht_batch_create); the check sorts a copy on the stack
+        const cht_table *seen[CHT_STATIC_BATCH_MAX];
+        std::copy(tables, tables + count, seen);
+        std::sort(seen, seen + count);
+        if (std::adjacent_find(seen, seen + count) != seen + count)
+            return fail(CHT_ERR_INVALID, "a find-or-put batch lists a table twice");
+    }
     void *dst = nullptr;
     int e = static_batch_address(cur, &dst);
     if (e) return e;

@@ -160,3 +160,17 @@ def test_static_batch_rejects_more_tables_than_its_array_holds():
     code, L = _static_call([t] * (limit + 1), [k] * (limit + 1), [s] * (limit + 1))
     assert code == _lib.CHT_ERR_INVALID
     assert b"1..256" in L.cht_last_error()
+
+
+def test_static_batch_rejects_a_table_listed_twice():
+    import paper_2406_09255_gb300 as m
+    from paper_2406_09255_gb300 import _lib
+    a = m.Table(m.ICEBERG, 32, 1 << 8, 1 << 5, key_bytes=4, fields_per_word=2, seed=1)
+    b = m.Table(m.ICEBERG, 32, 1 << 8, 1 << 5, key_bytes=4, fields_per_word=2, seed=2)
+    k = torch.ones(8, dtype=torch.int32, device=DEV)
+    s = torch.empty(8, dtype=torch.uint8, device=DEV)
+    code, L = _static_call([a, b, a], [k] * 3, [s] * 3)
+    assert code == _lib.CHT_ERR_INVALID
+    assert b"twice" in L.cht_last_error()
+    code, L = _static_call([a, b], [k] * 2, [s] * 2)
+    assert code == _lib.CHT_OK
