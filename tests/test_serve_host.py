@@ -113,6 +113,16 @@ def test_per_table_queues_match_the_plain_rule():
     assert [r.rid for r in wave] == [0, 1] and [r.rid for r in rest] == [2, 3, 4]
 
 
+def test_wave_request_cap():
+    """At most max_requests requests join a wave (a fused launch holds one
+    entry per request); the rest stay in arrival order."""
+    p = reqs([(i % 3, FIND, 1) for i in range(50)])
+    pq = PendingQueues(p)
+    wave = pq.form_wave(10 ** 9, max_requests=16)
+    assert [r.rid for r in wave] == list(range(16))
+    assert [r.rid for r in pq.requests()] == list(range(16, 50)) and len(pq) == 34
+
+
 def test_admission_wait_keeps_arrival_order_and_reject_drops():
     p = reqs([(0, FIND, 10), (1, FOP, 500), (2, FIND, 10), (3, FOP, 7)])
     verdicts = {0: OK, 1: WAIT, 2: OK, 3: OK}
